@@ -1,0 +1,147 @@
+"""CPU oracle for the constraint-checking pipeline -- TEST INFRASTRUCTURE.
+
+Only the tests, `__graft_entry__.smoke()` and the benchmark's CPU-baseline /
+reference leg may import this package.  The product (the CUDA library and its
+binding) never does, and it shares no code with it.
+
+* `ccpm_oracle.c`  -- plain single-threaded C: init (Alg. 3), one LCC round and
+  the LCC fixpoint (Alg. 4/5), one NLCC constraint (Alg. 6/7, as an injective
+  rooted-embedding search), final template-driven search with match counting
+  (Remark 1, Section 4.6).
+* `constraints.py` -- non-local constraint generation (Table 3, Alg. 2).
+* `pipeline.py`    -- the main loop (Alg. 1) over the pieces above.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ccpm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle in place with gcc -O2 (no OpenMP, one thread)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        i64, i32, u32p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        vp = ctypes.c_void_p
+        L.oracle_init.argtypes = [i64, vp, vp, vp, i32, vp, vp, vp]
+        L.oracle_init.restype = None
+        L.oracle_lcc_round.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_lcc_round.restype = ctypes.c_int
+        L.oracle_lcc.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp, vp]
+        L.oracle_lcc.restype = ctypes.c_int64
+        L.oracle_nlcc.argtypes = [i64, vp, vp, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp]
+        L.oracle_nlcc.restype = ctypes.c_int
+        L.oracle_final.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_uint64]
+        L.oracle_final.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def template_tables(labels, edges):
+    n0 = len(labels)
+    tlab = np.zeros(32, dtype=np.uint8)
+    tlab[:n0] = labels
+    tadj = np.zeros(32, dtype=np.uint32)
+    for a, b in edges:
+        tadj[a] |= np.uint32(1 << b)
+        tadj[b] |= np.uint32(1 << a)
+    return tlab, tadj
+
+
+class Graph:
+    """Contiguous views of a CSR graph as the C oracle wants them."""
+
+    def __init__(self, row_ptr, col, labels):
+        self.rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.lab = np.ascontiguousarray(labels, dtype=np.uint8)
+        self.n = int(self.rp.shape[0] - 1)
+        self.m = int(self.rp[-1])
+
+
+def init(g: Graph, labels, edges):
+    tlab, _ = template_tables(labels, edges)
+    omega = np.zeros(max(g.n, 1), dtype=np.uint32)[: g.n]
+    A = np.zeros(max(g.m, 1), dtype=np.uint8)[: g.m]
+    omega = np.ascontiguousarray(omega)
+    A = np.ascontiguousarray(A)
+    lib().oracle_init(g.n, _p(g.rp), _p(g.col), _p(g.lab), len(labels), _p(tlab), _p(omega), _p(A))
+    return omega, A
+
+
+def lcc_round(g: Graph, labels, edges, omega, A):
+    """One Jacobi LCC round.  Returns (changed, omega', A', scanned)."""
+    tlab, tadj = template_tables(labels, edges)
+    om2 = np.zeros_like(omega)
+    A2 = np.zeros_like(A)
+    sc = np.zeros(1, dtype=np.int64)
+    ch = lib().oracle_lcc_round(g.n, _p(g.rp), _p(g.col), len(labels), _p(tlab), _p(tadj),
+                                _p(omega), _p(A), _p(om2), _p(A2), _p(sc))
+    return bool(ch), om2, A2, int(sc[0])
+
+
+def lcc(g: Graph, labels, edges, omega, A):
+    """LCC to fixpoint in place.  Returns (rounds, scanned)."""
+    tlab, tadj = template_tables(labels, edges)
+    sc = np.zeros(1, dtype=np.int64)
+    r = lib().oracle_lcc(g.n, _p(g.rp), _p(g.col), len(labels), _p(tlab), _p(tadj),
+                         _p(omega), _p(A), _p(sc))
+    if r < 0:
+        raise MemoryError("oracle_lcc")
+    return int(r), int(sc[0])
+
+
+def nlcc(g: Graph, svert_mask: int, sadj, heads_mask: int, omega, A):
+    """One non-local constraint in place.  Returns (changed, tokens issued)."""
+    sadj = np.ascontiguousarray(np.asarray(list(sadj) + [0] * (32 - len(sadj)), dtype=np.uint32))
+    nt = np.zeros(1, dtype=np.int64)
+    ch = lib().oracle_nlcc(g.n, _p(g.rp), _p(g.col), svert_mask, _p(sadj), heads_mask,
+                           _p(omega), _p(A), _p(nt))
+    if ch < 0:
+        raise MemoryError("oracle_nlcc")
+    return bool(ch), int(nt[0])
+
+
+def final(g: Graph, labels, edges, omega, A, cap: int):
+    """Full template-driven search.  Returns (status, omega*, A*, count)."""
+    _, tadj = template_tables(labels, edges)
+    te = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    om2 = np.zeros_like(omega)
+    A2 = np.zeros_like(A)
+    cnt = np.zeros(1, dtype=np.uint64)
+    st = lib().oracle_final(g.n, _p(g.rp), _p(g.col), len(labels), _p(tadj), len(edges), _p(te),
+                            _p(omega), _p(A), _p(om2), _p(A2), _p(cnt), int(cap))
+    return int(st), om2, A2, int(cnt[0])
+
+
+def pack_bits(A: np.ndarray) -> np.ndarray:
+    """Byte-per-entry edge flags -> uint32 words, bit e&31 of word e>>5."""
+    m = A.shape[0]
+    words = (m + 31) // 32
+    b = np.packbits(A.astype(np.uint8), bitorder="little")
+    out = np.zeros(words * 4, dtype=np.uint8)
+    out[: b.shape[0]] = b
+    return out.view("<u4").astype(np.uint32)

@@ -1,0 +1,292 @@
+"""Seeded synthetic inputs: R-MAT background graphs, vertex labels and templates.
+
+This module only *generates inputs*; it holds none of the pruning arithmetic, so
+both the CUDA path and the CPU oracle consume its arrays unchanged.
+
+Background graphs follow the R-MAT recipe the paper uses for its synthetic runs
+(Section 6 "Datasets", and Section 6.8 for the three (A, B, C, D) skews):
+2^scale vertices, edge factor 16 directed draws, undirected by storing both
+directions, with self loops and duplicate edges removed.  Vertex labels are
+either degree-derived, l(v) = ceil(log2(d(v)+1)) (Section 6 "Datasets"), which
+is the bit length of d(v), or Zipf-distributed over a fixed label alphabet.
+
+Randomness: numpy's Philox counter-based bit generator, seeded explicitly, so
+the same seed gives the same graph on every machine.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+GRAPH500_ABCD = (0.57, 0.19, 0.19, 0.05)
+
+
+@dataclasses.dataclass
+class Graph:
+    """Undirected simple graph in CSR form (each undirected edge stored twice)."""
+    n: int
+    row_ptr: np.ndarray   # int64 [n+1]
+    col: np.ndarray       # int32 [m_dir], rows sorted ascending, no self loops
+    labels: np.ndarray    # uint8 [n]
+    name: str = ""
+
+    @property
+    def m_dir(self) -> int:
+        return int(self.col.shape[0])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+@dataclasses.dataclass
+class Template:
+    """Small connected template G0: n0 vertices, labels, undirected edge list."""
+    labels: list
+    edges: list           # list of (a, b) with a != b, each undirected edge once
+    name: str = ""
+
+    @property
+    def n0(self) -> int:
+        return len(self.labels)
+
+    @property
+    def m0(self) -> int:
+        return len(self.edges)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def rmat_edges(scale: int, edge_factor: int = 16, abcd=GRAPH500_ABCD,
+               seed: int = 1, chunk: int = 1 << 24):
+    """Draw edge_factor * 2^scale directed R-MAT edges (src, dst) as uint32.
+
+    At every one of the `scale` levels an edge picks one quadrant with
+    probabilities (A, B, C, D), D = 1 - A - B - C, with no noise.  The vertex ids
+    are then relabelled by a seeded random permutation (Graph 500 style) so
+    that vertex id carries no degree information.
+    """
+    a, b, c = abcd[0], abcd[1], abcd[2]
+    n = 1 << scale
+    m = edge_factor * n
+    t_a = np.uint32(min(int(a * 2**32), 2**32 - 1))
+    t_ab = np.uint32(min(int((a + b) * 2**32), 2**32 - 1))
+    t_abc = np.uint32(min(int((a + b + c) * 2**32), 2**32 - 1))
+    rng = _rng(seed)
+    src = np.zeros(m, dtype=np.uint32)
+    dst = np.zeros(m, dtype=np.uint32)
+    for lo in range(0, m, chunk):
+        hi = min(m, lo + chunk)
+        s = np.zeros(hi - lo, dtype=np.uint32)
+        d = np.zeros(hi - lo, dtype=np.uint32)
+        raw = None
+        for level in range(scale):
+            # two 32-bit draws per 64-bit Philox output
+            if level % 2 == 0:
+                raw = rng.bit_generator.random_raw(hi - lo)
+                r = (raw & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+            else:
+                r = (raw >> np.uint64(32)).astype(np.uint32)
+            sbit = (r >= t_ab)
+            dbit = ((r >= t_a) & (r < t_ab)) | (r >= t_abc)
+            s |= sbit.astype(np.uint32) << np.uint32(level)
+            d |= dbit.astype(np.uint32) << np.uint32(level)
+        src[lo:hi] = s
+        dst[lo:hi] = d
+    perm = _rng(seed ^ 0x5EED).permutation(n).astype(np.uint32)
+    return perm[src], perm[dst]
+
+
+def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, device=None):
+    """Symmetrise, drop self loops, deduplicate and sort into CSR.
+
+    `device` optionally names a torch CUDA device used only to sort the keys
+    faster; the result is identical either way (a sort is exact).
+    """
+    keep = src != dst
+    s = src[keep].astype(np.int64)
+    d = dst[keep].astype(np.int64)
+    keys = np.concatenate([s * n + d, d * n + s])
+    del s, d
+    if device is not None:
+        import torch
+        t = torch.from_numpy(keys).to(device)
+        t = torch.unique(t, sorted=True)
+        keys = t.cpu().numpy()
+        del t
+    else:
+        keys.sort()
+        if keys.shape[0]:
+            keep = np.empty(keys.shape[0], dtype=bool)
+            keep[0] = True
+            np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+            keys = keys[keep]
+    rows = keys // n
+    col = (keys - rows * n).astype(np.int32)
+    counts = np.bincount(rows, minlength=n).astype(np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, col
+
+
+def degree_labels(row_ptr: np.ndarray) -> np.ndarray:
+    """l(v) = ceil(log2(d+1)) = bit length of d (0 for an isolated vertex)."""
+    d = np.diff(row_ptr).astype(np.int64)
+    lab = np.zeros(d.shape[0], dtype=np.uint8)
+    x = d.copy()
+    while np.any(x > 0):
+        nz = x > 0
+        lab[nz] += 1
+        x >>= 1
+    return lab
+
+
+def zipf_labels(n: int, n_labels: int = 64, s: float = 1.2, seed: int = 7) -> np.ndarray:
+    """iid labels with P(k) proportional to (k+1)^-s, k = 0..n_labels-1."""
+    w = (np.arange(n_labels, dtype=np.float64) + 1.0) ** (-s)
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+    u = _rng(seed).random(n)
+    return np.searchsorted(cdf, u, side="right").astype(np.uint8)
+
+
+def rmat_graph(scale: int, edge_factor: int = 16, abcd=GRAPH500_ABCD, seed: int = 1,
+               labels: str = "degree", n_labels: int = 64, zipf_s: float = 1.2,
+               label_seed: int = 7, device=None) -> Graph:
+    n = 1 << scale
+    src, dst = rmat_edges(scale, edge_factor, abcd, seed)
+    row_ptr, col = csr_from_edges(n, src, dst, device=device)
+    del src, dst
+    if labels == "degree":
+        lab = degree_labels(row_ptr)
+    elif labels == "zipf":
+        lab = zipf_labels(n, n_labels, zipf_s, label_seed)
+    else:
+        raise ValueError(labels)
+    return Graph(n, row_ptr, col, lab, name=f"rmat{scale}-{labels}")
+
+
+def graph_from_edge_list(n: int, edges, labels) -> Graph:
+    """Small hand-built graphs (tests): undirected edge list -> CSR."""
+    e = np.asarray(list(edges), dtype=np.int64).reshape(-1, 2)
+    src = e[:, 0].astype(np.uint32)
+    dst = e[:, 1].astype(np.uint32)
+    row_ptr, col = csr_from_edges(n, src, dst)
+    return Graph(n, row_ptr, col, np.asarray(labels, dtype=np.uint8))
+
+
+def label_frequencies(g: Graph, n_labels: int = 256) -> np.ndarray:
+    return np.bincount(g.labels, minlength=n_labels)[:n_labels].astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Templates
+# ---------------------------------------------------------------------------
+
+def is_connected(n0: int, edges) -> bool:
+    adj = [set() for _ in range(n0)]
+    for a, b in edges:
+        adj[a].add(b)
+        adj[b].add(a)
+    seen = {0}
+    stack = [0]
+    while stack:
+        x = stack.pop()
+        for y in adj[x]:
+            if y not in seen:
+                seen.add(y)
+                stack.append(y)
+    return len(seen) == n0
+
+
+def random_template(seed: int, n0: int, extra_edges: int, label_pool,
+                    label_weights=None) -> Template:
+    """Random connected template: a random spanning tree plus `extra_edges`
+    chords, labels drawn from `label_pool` (optionally weighted)."""
+    rng = _rng(seed)
+    edges = set()
+    for v in range(1, n0):
+        u = int(rng.integers(0, v))
+        edges.add((u, v))
+    possible = [(a, b) for a in range(n0) for b in range(a + 1, n0) if (a, b) not in edges]
+    rng.shuffle(possible)
+    for e in possible[:extra_edges]:
+        edges.add(tuple(e))
+    pool = np.asarray(label_pool)
+    p = None
+    if label_weights is not None:
+        p = np.asarray(label_weights, dtype=np.float64)
+        p = p / p.sum()
+    labs = [int(x) for x in rng.choice(pool, size=n0, p=p)]
+    return Template(labs, sorted(edges), name=f"rand{seed}")
+
+
+def edit_variants(base: Template, count: int, seed: int, label_pool,
+                  max_k: int = 2, n_min: int = 5, n_max: int = 9):
+    """Edit-distance variants of `base` for the exploratory-search workload
+    (Section 7.2): each variant applies k in {1, 2} random edits drawn from
+    {delete an edge keeping the template connected, add an edge, delete a
+    leaf, add a leaf}.  Variants keep 5..9 vertices; duplicates are allowed."""
+    rng = _rng(seed)
+    out = []
+    tries = 0
+    while len(out) < count and tries < count * 200:
+        tries += 1
+        labels = list(base.labels)
+        edges = set(tuple(sorted(e)) for e in base.edges)
+        k = int(rng.integers(1, max_k + 1))
+        ok = True
+        for _ in range(k):
+            op = int(rng.integers(0, 4))
+            n0 = len(labels)
+            if op == 0:     # delete an edge, keep connected
+                cand = sorted(edges)
+                rng.shuffle(cand)
+                done = False
+                for e in cand:
+                    trial = edges - {e}
+                    if is_connected(n0, trial):
+                        edges = trial
+                        done = True
+                        break
+                ok &= done
+            elif op == 1:   # add an edge
+                cand = [(a, b) for a in range(n0) for b in range(a + 1, n0) if (a, b) not in edges]
+                if not cand:
+                    ok = False
+                    break
+                edges.add(cand[int(rng.integers(0, len(cand)))])
+            elif op == 2:   # delete a leaf
+                deg = [0] * n0
+                for a, b in edges:
+                    deg[a] += 1
+                    deg[b] += 1
+                leaves = [v for v in range(n0) if deg[v] == 1]
+                if not leaves or n0 <= n_min:
+                    ok = False
+                    break
+                x = leaves[int(rng.integers(0, len(leaves)))]
+                edges = set((a - (a > x), b - (b > x)) for a, b in edges if x not in (a, b))
+                labels = labels[:x] + labels[x + 1:]
+            else:           # add a leaf
+                if n0 >= n_max:
+                    ok = False
+                    break
+                u = int(rng.integers(0, n0))
+                labels.append(int(label_pool[int(rng.integers(0, len(label_pool)))]))
+                edges.add((u, n0))
+        if not ok:
+            continue
+        n0 = len(labels)
+        if not (n_min <= n0 <= n_max) or not is_connected(n0, edges):
+            continue
+        out.append(Template(labels, sorted(edges), name=f"{base.name}-ed{len(out)}"))
+    return out
+
+
+def labels_by_frequency(g: Graph):
+    """Labels sorted from most to least frequent (ties: smaller label first)."""
+    f = label_frequencies(g)
+    order = sorted(range(len(f)), key=lambda L: (-f[L], L))
+    return [L for L in order if f[L] > 0]
