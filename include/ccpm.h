@@ -1,0 +1,198 @@
+/*
+ * ccpm.h -- C ABI of the GB300 constraint-checking pattern matcher.
+ *
+ * The library prunes a vertex-labelled background graph G down to exactly the
+ * vertices and edges that take part in at least one exact match of a small
+ * connected template G0 (Definition 1 of "Scalable Pattern Matching in
+ * Metadata Graphs via Constraint Checking"): local constraint checking to a
+ * fixpoint (Alg. 4), one non-local constraint at a time with LCC re-run after
+ * any change (Alg. 1, Alg. 6/7), and a final template-driven search over the
+ * whole template (Remark 1, Section 4.6) that also counts matches.
+ *
+ * Conventions
+ *   - Every call returns an int status (CCPM_OK or a CCPM_E* code); no C++
+ *     exception crosses this boundary.  ccpm_last_error() gives a message.
+ *   - Graph layout: undirected simple graph in CSR, each undirected edge stored
+ *     in both rows; row_ptr is int64 [n+1], col is int32 [m_dir] with every row
+ *     sorted ascending, no self loops, no duplicates.  labels is uint8 [n].
+ *   - omega layout: uint32 per vertex; bit q set <=> template vertex q is a
+ *     possible match of that vertex (omega(v) of Section 2).
+ *   - Edge bitmap layout: one bit per CSR entry e, bit (e & 31) of word e >> 5
+ *     (uint32 words, ceil(m_dir / 32) of them); both directions of an
+ *     undirected edge always carry the same value.
+ *   - Calls run on the context's CUDA stream and return after the work they
+ *     describe has completed, unless stated otherwise.
+ *   - All handles are single-thread objects: do not use one handle from two
+ *     host threads at once.
+ */
+#ifndef CCPM_H
+#define CCPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCPM_OK        0
+#define CCPM_EINVAL    1   /* bad argument, bad CSR, bad template             */
+#define CCPM_ENOMEM    2   /* host or device allocation failed                 */
+#define CCPM_ECUDA     3   /* a CUDA runtime call failed                       */
+#define CCPM_ETIMEOUT  4   /* a device-side wait gave up (bounded spin)        */
+#define CCPM_EOVERFLOW 5   /* a fixed-capacity device buffer would overflow    */
+#define CCPM_EBUDGET   6   /* a search budget was exceeded; see ccpm_counts    */
+#define CCPM_ESTATE    7   /* call made in the wrong order                     */
+
+/* ccpm_graph_load_csr flags */
+#define CCPM_HOST_PTRS    0  /* pointers are host memory; the library copies them     */
+#define CCPM_DEVICE_PTRS  1  /* pointers are device memory on the context's device,
+                                borrowed: they must stay valid until the graph is
+                                destroyed and must not be modified meanwhile       */
+#define CCPM_VALIDATE     2  /* check sortedness, symmetry, self loops, duplicates */
+
+#define CCPM_MAX_TMPL_VERTICES 32
+#define CCPM_MAX_TMPL_EDGES    496
+
+/* constraint kinds (Table 3): path, cycle, and the three TDS unions */
+#define CCPM_KIND_PC     0
+#define CCPM_KIND_CC     1
+#define CCPM_KIND_TDS_CC 2
+#define CCPM_KIND_TDS_PC 3
+#define CCPM_KIND_TDS    4
+
+/* constraint order (Section 3.2 "Constraint Ordering Heuristics") */
+#define CCPM_ORDER_FIXED    0  /* the paper's heuristic: paths and cycles first, shorter first */
+#define CCPM_ORDER_EXPLICIT 1  /* the order given by ccpm_tmpl_set_order                       */
+
+typedef struct ccpm_ctx    *ccpm_ctx_t;
+typedef struct ccpm_graph  *ccpm_graph_t;
+typedef struct ccpm_tmpl   *ccpm_tmpl_t;
+typedef struct ccpm_result *ccpm_result_t;
+
+typedef struct {
+    int      kind;                 /* CCPM_KIND_*                                  */
+    int      n_verts;              /* |V_S|                                        */
+    uint32_t vert_mask;            /* bit q: template vertex q is in S             */
+    uint32_t head_mask;            /* template vertices whose matches issue tokens */
+    int      n_edges;              /* |E_S|                                        */
+    int32_t  edges[CCPM_MAX_TMPL_EDGES][2];   /* (a, b), a < b, sorted             */
+} ccpm_constraint_info;
+
+typedef struct {
+    int      order_mode;           /* CCPM_ORDER_*                                  */
+    int      run_final;            /* 1 (default): final exact search + counting   */
+    uint64_t max_embeddings;       /* final search stops past this many matches    */
+    uint64_t search_budget;        /* max 32-candidate windows one root may scan;  */
+                                   /* 0 = library default                          */
+    int      hub_degree;           /* rows longer than this are split across warps;*/
+                                   /* 0 = library default                          */
+    int      reserved[8];
+} ccpm_options;
+
+typedef struct {
+    int64_t  active_v;             /* vertices with omega != 0 at the end         */
+    int64_t  active_e_dir;         /* set bits in the edge bitmap (2 x |E*|)      */
+    int64_t  lcc_rounds_total;     /* LCC rounds over all phases, each phase      */
+                                   /* counting its final quiescent round          */
+    int32_t  n_phases;             /* 1 + number of non-local constraints         */
+    int32_t  nlcc_constraints_run;
+    uint64_t match_embeddings;     /* number of matches phi (valid if count_valid)*/
+    uint64_t automorphisms;        /* label-preserving automorphisms of G0        */
+    uint64_t match_subgraphs;      /* match_embeddings / automorphisms            */
+    int32_t  count_valid;          /* 0 if the final search hit a budget          */
+    int32_t  status;               /* status of the prune call                    */
+    int64_t  tokens;               /* (vertex, head) token walks issued by NLCC   */
+    int64_t  edges_scanned_lcc;    /* sum over LCC rounds of active CSR entries   */
+    int64_t  edges_scanned_search; /* CSR entries examined by NLCC + final search */
+    double   ms_total, ms_lcc, ms_nlcc, ms_final;   /* device time per stage     */
+    /* measurement of the LCC round kernel (CUDA events around each launch on
+     * the context stream) and its algorithmic traffic:
+     *   24 B per active vertex (two int64 row offsets, omega read and write)
+     * + 4.125 B per CSR entry of an active row (column index, edge bit)
+     * + 4 B per active entry (gather of the neighbour's omega)              */
+    int64_t  lcc_launches;
+    double   ms_lcc_kernel;
+    int64_t  lcc_alg_bytes;
+    int64_t  lcc_row_entries;      /* CSR entries in rows of active vertices  */
+    int64_t  lcc_active_vertices;  /* active vertices, summed over rounds      */
+    int64_t  kernel_launches;      /* all kernels this call launched          */
+} ccpm_counts;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA `device`.  `cuda_stream` (a cudaStream_t) may be
+ * NULL, in which case the library creates and owns a stream.  A non-NULL
+ * stream is borrowed and must outlive the context. */
+int  ccpm_ctx_create(int device, void *cuda_stream, ccpm_ctx_t *out);
+void ccpm_ctx_destroy(ccpm_ctx_t ctx);
+/* Message for the last failing call on this context (never NULL). */
+const char *ccpm_last_error(ccpm_ctx_t ctx);
+void ccpm_options_default(ccpm_options *opt);
+
+/* ------------------------------------------------------------------ graph */
+
+/* Load the background graph G (Section 2; CSR + separate label store as in
+ * Section 4.7).  n vertices, m_dir directed CSR entries.  With
+ * CCPM_HOST_PTRS the arrays are copied to the device; with CCPM_DEVICE_PTRS
+ * they are borrowed.  CCPM_VALIDATE adds an O(m) host check (host pointers
+ * only) and returns CCPM_EINVAL on an unsorted row, self loop, duplicate or a
+ * missing reverse entry.  n must be < 2^31. */
+int  ccpm_graph_load_csr(ccpm_ctx_t ctx, int64_t n, int64_t m_dir,
+                         const int64_t *row_ptr, const int32_t *col,
+                         const uint8_t *labels, int flags, ccpm_graph_t *out);
+void ccpm_graph_destroy(ccpm_graph_t g);
+
+/* --------------------------------------------------------------- template */
+
+/* Load template G0 (Section 2): n0 in [2, 32] vertices with labels, m0
+ * undirected edges given as 2*m0 int32 (a, b) pairs.  CCPM_EINVAL if G0 is
+ * disconnected (Section 2 assumes connected), has a self loop, a duplicate or
+ * an out-of-range vertex. */
+int  ccpm_tmpl_load(ccpm_ctx_t ctx, int n0, const uint8_t *labels, int m0,
+                    const int32_t *edges, ccpm_tmpl_t *out);
+void ccpm_tmpl_destroy(ccpm_tmpl_t t);
+
+/* Generate the ordered non-local constraint set K0 (Table 3 Steps 1-5,
+ * Alg. 2, ordering of Section 3.2).  The graph supplies background label
+ * frequencies used to orient token walks (Section 3.2 "Constraint
+ * Optimization"); it may be NULL.  Writes |K0| to *n_constraints. */
+int  ccpm_constraints_generate(ccpm_tmpl_t t, ccpm_graph_t g, int *n_constraints);
+/* Describe constraint i (0-based, in the current order). */
+int  ccpm_constraints_describe(ccpm_tmpl_t t, int i, ccpm_constraint_info *out);
+/* Explicit order: order[j] = index (in the generated order) of the constraint
+ * to check j-th; must be a permutation of 0..n-1.  Used with
+ * CCPM_ORDER_EXPLICIT. */
+int  ccpm_tmpl_set_order(ccpm_tmpl_t t, int n, const int32_t *order);
+
+/* ------------------------------------------------------------------ prune */
+
+/* Run the whole pipeline (Alg. 1 plus the final search) for template t over
+ * graph g.  If *out is NULL a result is created; a non-NULL *out made by an
+ * earlier call on the same graph is reused (its buffers are overwritten).
+ * Returns CCPM_OK, CCPM_EBUDGET (results still valid as a superset of the
+ * exact answer when the final search stopped early: count_valid = 0), or an
+ * error. */
+int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
+                const ccpm_options *opt, ccpm_result_t *out);
+
+/* ----------------------------------------------------------------- result */
+
+/* Copy omega (n uint32) to dst (host memory, or device memory when
+ * dst_on_device != 0). */
+int  ccpm_result_omega(ccpm_result_t r, uint32_t *dst, int64_t n, int dst_on_device);
+/* Copy the edge bitmap (ceil(m_dir/32) words) to dst. */
+int  ccpm_result_edge_bitmap(ccpm_result_t r, uint32_t *dst, int64_t words, int dst_on_device);
+int  ccpm_result_counts(ccpm_result_t r, ccpm_counts *out);
+/* LCC rounds per phase: [initial LCC, after constraint 1, ...]; a phase whose
+ * constraint changed nothing has 0 rounds.  Writes min(cap, n_phases). */
+int  ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap);
+/* Device pointers owned by the result (valid until it is destroyed). */
+const uint32_t *ccpm_result_omega_device(ccpm_result_t r);
+const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r);
+void ccpm_result_destroy(ccpm_result_t r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCPM_H */

@@ -47,9 +47,9 @@ def lib():
         L.oracle_lcc_round.restype = ctypes.c_int
         L.oracle_lcc.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp, vp]
         L.oracle_lcc.restype = ctypes.c_int64
-        L.oracle_nlcc.argtypes = [i64, vp, vp, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp]
+        L.oracle_nlcc.argtypes = [i64, vp, vp, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp, vp]
         L.oracle_nlcc.restype = ctypes.c_int
-        L.oracle_final.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_uint64]
+        L.oracle_final.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, vp]
         L.oracle_final.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -114,26 +114,34 @@ def lcc(g: Graph, labels, edges, omega, A):
     return int(r), int(sc[0])
 
 
-def nlcc(g: Graph, svert_mask: int, sadj, heads_mask: int, omega, A):
-    """One non-local constraint in place.  Returns (changed, tokens issued)."""
+def nlcc(g: Graph, svert_mask: int, sadj, heads_mask: int, omega, A, with_scanned=False):
+    """One non-local constraint in place.  Returns (changed, tokens issued[,
+    CSR entries examined])."""
     sadj = np.ascontiguousarray(np.asarray(list(sadj) + [0] * (32 - len(sadj)), dtype=np.uint32))
     nt = np.zeros(1, dtype=np.int64)
+    ns = np.zeros(1, dtype=np.int64)
     ch = lib().oracle_nlcc(g.n, _p(g.rp), _p(g.col), svert_mask, _p(sadj), heads_mask,
-                           _p(omega), _p(A), _p(nt))
+                           _p(omega), _p(A), _p(nt), _p(ns))
     if ch < 0:
         raise MemoryError("oracle_nlcc")
+    if with_scanned:
+        return bool(ch), int(nt[0]), int(ns[0])
     return bool(ch), int(nt[0])
 
 
-def final(g: Graph, labels, edges, omega, A, cap: int):
-    """Full template-driven search.  Returns (status, omega*, A*, count)."""
+def final(g: Graph, labels, edges, omega, A, cap: int, with_scanned=False):
+    """Full template-driven search.  Returns (status, omega*, A*, count[,
+    CSR entries examined])."""
     _, tadj = template_tables(labels, edges)
     te = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
     om2 = np.zeros_like(omega)
     A2 = np.zeros_like(A)
     cnt = np.zeros(1, dtype=np.uint64)
+    ns = np.zeros(1, dtype=np.int64)
     st = lib().oracle_final(g.n, _p(g.rp), _p(g.col), len(labels), _p(tadj), len(edges), _p(te),
-                            _p(omega), _p(A), _p(om2), _p(A2), _p(cnt), int(cap))
+                            _p(omega), _p(A), _p(om2), _p(A2), _p(cnt), int(cap), _p(ns))
+    if with_scanned:
+        return int(st), om2, A2, int(cnt[0]), int(ns[0])
     return int(st), om2, A2, int(cnt[0])
 
 

@@ -185,6 +185,7 @@ typedef struct {
     int64_t psi[32];       /* current partial map: template id -> background vertex */
     /* enumeration outputs (final step only) */
     int enumerate;
+    int64_t scanned;       /* CSR entries examined (edges-scanned metric) */
     uint64_t count;
     uint64_t cap;
     int over_budget;
@@ -232,6 +233,7 @@ static int extend(search_t *s, int i)
     int q = s->order[i];
     int64_t anchor = s->psi[s->parent[i]];
     for (int64_t e = s->rp[anchor]; e < s->rp[anchor + 1]; e++) {
+        s->scanned++;
         if (!s->A[e]) continue;
         int64_t u = s->col[e];
         if (!((s->omega[u] >> q) & 1u)) continue;
@@ -265,7 +267,7 @@ static int extend(search_t *s, int i)
 /* ------------------------------------------------------------------------ */
 int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
                 uint32_t svert, const uint32_t *sadj, uint32_t heads,
-                uint32_t *omega, uint8_t *A, int64_t *n_tokens)
+                uint32_t *omega, uint8_t *A, int64_t *n_tokens, int64_t *n_scanned)
 {
     int64_t m = rp[n];
     uint32_t *om0 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
@@ -300,6 +302,7 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
             }
         }
     }
+    *n_scanned += s.scanned;
     free(om0);
     free(A0);
     return changed;
@@ -318,7 +321,8 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
 int oracle_final(int64_t n, const int64_t *rp, const int32_t *col,
                  int n0, const uint32_t *tadj, int m0, const int32_t *tedges,
                  const uint32_t *omega, const uint8_t *A,
-                 uint32_t *om_out, uint8_t *A_out, uint64_t *count, uint64_t cap)
+                 uint32_t *om_out, uint8_t *A_out, uint64_t *count, uint64_t cap,
+                 int64_t *n_scanned)
 {
     int64_t m = rp[n];
     memset(om_out, 0, sizeof(uint32_t) * (size_t)n);
@@ -338,5 +342,6 @@ int oracle_final(int64_t n, const int64_t *rp, const int32_t *col,
         extend(&s, 1);
     }
     *count = s.count;
+    *n_scanned += s.scanned;
     return s.over_budget ? OR_EBUDGET : OR_OK;
 }

@@ -32,6 +32,7 @@ class OracleResult:
     active_e_dir: int
     lcc_scanned: int             # sum over rounds of active entries at round start
     tokens: int
+    search_scanned: int = 0      # CSR entries examined by the searches (metric only)
     seconds: float = 0.0
     omega_pre_final: np.ndarray = None
     A_pre_final: np.ndarray = None
@@ -88,9 +89,11 @@ def run(row_ptr, col, labels, tlabels, tedges, constraints=None,
     phase = [r]
     changed_list = []
     tokens = 0
+    search_scanned = 0
     for c in constraints:
-        ch, nt = nlcc(g, c.vmask(), c.sadj(len(tlabels)), c.hmask(), omega, A)
+        ch, nt, ns = nlcc(g, c.vmask(), c.sadj(len(tlabels)), c.hmask(), omega, A, with_scanned=True)
         tokens += nt
+        search_scanned += ns
         changed_list.append(ch)
         if ch:
             r, sc = lcc(g, tlabels, tedges, omega, A)
@@ -99,7 +102,8 @@ def run(row_ptr, col, labels, tlabels, tedges, constraints=None,
             r = 0
         phase.append(r)
     om_pre, A_pre = omega.copy(), A.copy()
-    st, om_f, A_f, count = final(g, tlabels, tedges, omega, A, max_embeddings)
+    st, om_f, A_f, count, ns = final(g, tlabels, tedges, omega, A, max_embeddings, with_scanned=True)
+    search_scanned += ns
     valid = st == 0
     if valid:
         omega, A = om_f, A_f
@@ -108,6 +112,6 @@ def run(row_ptr, col, labels, tlabels, tedges, constraints=None,
         nlcc_changed=changed_list, match_embeddings=count if valid else 0,
         count_valid=valid, automorphisms=automorphisms(tlabels, tedges),
         active_v=int(np.count_nonzero(omega)), active_e_dir=int(np.count_nonzero(A)),
-        lcc_scanned=scanned, tokens=tokens, omega_pre_final=om_pre, A_pre_final=A_pre)
+        lcc_scanned=scanned, tokens=tokens, search_scanned=search_scanned, omega_pre_final=om_pre, A_pre_final=A_pre)
     res.seconds = time.perf_counter() - t0
     return res

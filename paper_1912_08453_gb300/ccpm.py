@@ -1,0 +1,295 @@
+"""Thin ctypes binding of the C ABI in include/ccpm.h.
+
+Argument marshalling only: every step of the pruning pipeline runs in the CUDA
+library `libccpm.so`.  There is no CPU fallback; if the library is missing the
+import of this module fails with a RuntimeError.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); CUDA tensors are passed as borrowed device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libccpm.so")
+
+CCPM_OK, CCPM_EINVAL, CCPM_ENOMEM, CCPM_ECUDA = 0, 1, 2, 3
+CCPM_ETIMEOUT, CCPM_EOVERFLOW, CCPM_EBUDGET, CCPM_ESTATE = 4, 5, 6, 7
+CCPM_HOST_PTRS, CCPM_DEVICE_PTRS, CCPM_VALIDATE = 0, 1, 2
+CCPM_ORDER_FIXED, CCPM_ORDER_EXPLICIT = 0, 1
+KIND_NAMES = {0: "PC", 1: "CC", 2: "TDS_CC", 3: "TDS_PC", 4: "TDS"}
+MAX_TMPL_EDGES = 496
+
+
+class CcpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ccpm error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("order_mode", ctypes.c_int), ("run_final", ctypes.c_int),
+                ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
+                ("hub_degree", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [("active_v", ctypes.c_int64), ("active_e_dir", ctypes.c_int64),
+                ("lcc_rounds_total", ctypes.c_int64), ("n_phases", ctypes.c_int32),
+                ("nlcc_constraints_run", ctypes.c_int32), ("match_embeddings", ctypes.c_uint64),
+                ("automorphisms", ctypes.c_uint64), ("match_subgraphs", ctypes.c_uint64),
+                ("count_valid", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("tokens", ctypes.c_int64), ("edges_scanned_lcc", ctypes.c_int64),
+                ("edges_scanned_search", ctypes.c_int64), ("ms_total", ctypes.c_double),
+                ("ms_lcc", ctypes.c_double), ("ms_nlcc", ctypes.c_double), ("ms_final", ctypes.c_double),
+                ("lcc_launches", ctypes.c_int64), ("ms_lcc_kernel", ctypes.c_double),
+                ("lcc_alg_bytes", ctypes.c_int64), ("lcc_row_entries", ctypes.c_int64),
+                ("lcc_active_vertices", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ConstraintInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_verts", ctypes.c_int), ("vert_mask", ctypes.c_uint32),
+                ("head_mask", ctypes.c_uint32), ("n_edges", ctypes.c_int),
+                ("edges", (ctypes.c_int32 * 2) * MAX_TMPL_EDGES)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_1912_08453_gb300.build.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "ccpm_ctx_create": ([i32, vp, P(vp)], i32),
+        "ccpm_ctx_destroy": ([vp], None),
+        "ccpm_last_error": ([vp], ctypes.c_char_p),
+        "ccpm_options_default": ([P(Options)], None),
+        "ccpm_graph_load_csr": ([vp, i64, i64, vp, vp, vp, i32, P(vp)], i32),
+        "ccpm_graph_destroy": ([vp], None),
+        "ccpm_tmpl_load": ([vp, i32, vp, i32, vp, P(vp)], i32),
+        "ccpm_tmpl_destroy": ([vp], None),
+        "ccpm_constraints_generate": ([vp, vp, P(i32)], i32),
+        "ccpm_constraints_describe": ([vp, i32, P(ConstraintInfo)], i32),
+        "ccpm_tmpl_set_order": ([vp, i32, vp], i32),
+        "ccpm_prune": ([vp, vp, vp, P(Options), P(vp)], i32),
+        "ccpm_result_omega": ([vp, vp, i64, i32], i32),
+        "ccpm_result_edge_bitmap": ([vp, vp, i64, i32], i32),
+        "ccpm_result_counts": ([vp, P(Counts)], i32),
+        "ccpm_result_phase_rounds": ([vp, vp, i32], i32),
+        "ccpm_result_omega_device": ([vp], vp),
+        "ccpm_result_edge_bitmap_device": ([vp], vp),
+        "ccpm_result_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+# every function the header declares (tests check the library exports them)
+EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_options_default",
+            "ccpm_graph_load_csr", "ccpm_graph_destroy", "ccpm_tmpl_load", "ccpm_tmpl_destroy",
+            "ccpm_constraints_generate", "ccpm_constraints_describe", "ccpm_tmpl_set_order",
+            "ccpm_prune", "ccpm_result_omega", "ccpm_result_edge_bitmap", "ccpm_result_counts",
+            "ccpm_result_phase_rounds", "ccpm_result_omega_device",
+            "ccpm_result_edge_bitmap_device", "ccpm_result_destroy"]
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(a.ctypes.data), False
+    import torch
+    if isinstance(a, torch.Tensor):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr()), a.is_cuda
+    raise TypeError(type(a))
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib.ccpm_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream)) if stream is not None else None
+        rc = lib.ccpm_ctx_create(device, s, ctypes.byref(h))
+        if rc:
+            raise CcpmError(rc, f"ccpm_ctx_create(device={device}) failed")
+        self.h = h
+        self.device = device
+
+    def check(self, rc, what=""):
+        if rc:
+            raise CcpmError(rc, f"{what}: {lib.ccpm_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            lib.ccpm_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A resident background graph (CSR + labels) on the context's device."""
+
+    def __init__(self, ctx: Context, row_ptr, col, labels, validate: bool = False):
+        p_rp, d0 = _ptr(row_ptr)
+        p_col, d1 = _ptr(col)
+        p_lab, d2 = _ptr(labels)
+        if not (d0 == d1 == d2):
+            raise ValueError("row_ptr, col and labels must all be host or all device arrays")
+        flags = CCPM_DEVICE_PTRS if d0 else CCPM_HOST_PTRS
+        if validate:
+            flags |= CCPM_VALIDATE
+        n = int(row_ptr.shape[0]) - 1
+        m = int(col.shape[0])
+        h = ctypes.c_void_p()
+        ctx.check(lib.ccpm_graph_load_csr(ctx.h, n, m, p_rp, p_col, p_lab, flags, ctypes.byref(h)),
+                  "ccpm_graph_load_csr")
+        self.h, self.ctx, self.n, self.m = h, ctx, n, m
+        self.words = (m + 31) // 32
+        self._keep = (row_ptr, col, labels) if d0 else None
+
+    def close(self):
+        if self.h:
+            lib.ccpm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Template:
+    def __init__(self, ctx, labels, edges):
+        lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8))
+        ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+        h = ctypes.c_void_p()
+        rc = lib.ccpm_tmpl_load(ctx.h if ctx else None, int(lab.shape[0]), _ptr(lab)[0],
+                                int(ed.shape[0] // 2), _ptr(ed)[0], ctypes.byref(h))
+        if rc:
+            msg = lib.ccpm_last_error(ctx.h).decode() if ctx else "invalid template"
+            raise CcpmError(rc, f"ccpm_tmpl_load: {msg}")
+        self.h, self.ctx = h, ctx
+        self.labels = [int(x) for x in lab]
+        self.edges = [tuple(int(v) for v in e) for e in np.asarray(edges).reshape(-1, 2)]
+
+    def generate(self, graph: Graph | None = None) -> int:
+        n = ctypes.c_int()
+        rc = lib.ccpm_constraints_generate(self.h, graph.h if graph else None, ctypes.byref(n))
+        if rc:
+            raise CcpmError(rc, "ccpm_constraints_generate")
+        return n.value
+
+    def describe(self, i: int) -> dict:
+        info = ConstraintInfo()
+        rc = lib.ccpm_constraints_describe(self.h, i, ctypes.byref(info))
+        if rc:
+            raise CcpmError(rc, "ccpm_constraints_describe")
+        verts = [q for q in range(32) if (info.vert_mask >> q) & 1]
+        heads = [q for q in range(32) if (info.head_mask >> q) & 1]
+        edges = [[info.edges[k][0], info.edges[k][1]] for k in range(info.n_edges)]
+        return {"kind": KIND_NAMES[info.kind], "verts": verts, "edges": edges, "heads": heads,
+                "vert_mask": info.vert_mask, "head_mask": info.head_mask}
+
+    def constraints(self):
+        n = self.generate()
+        return [self.describe(i) for i in range(n)]
+
+    def set_order(self, order):
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        rc = lib.ccpm_tmpl_set_order(self.h, int(o.shape[0]), _ptr(o)[0])
+        if rc:
+            raise CcpmError(rc, "ccpm_tmpl_set_order")
+
+    def close(self):
+        if self.h:
+            lib.ccpm_tmpl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    def __init__(self, graph: Graph, h):
+        self.graph, self.h = graph, h
+
+    def omega(self, out=None):
+        if out is None:
+            out = np.zeros(self.graph.n, dtype=np.uint32)
+        p, dev = _ptr(out)
+        self.graph.ctx.check(lib.ccpm_result_omega(self.h, p, self.graph.n, int(dev)), "ccpm_result_omega")
+        return out
+
+    def edge_bitmap(self, out=None):
+        if out is None:
+            out = np.zeros(self.graph.words, dtype=np.uint32)
+        p, dev = _ptr(out)
+        self.graph.ctx.check(lib.ccpm_result_edge_bitmap(self.h, p, self.graph.words, int(dev)),
+                             "ccpm_result_edge_bitmap")
+        return out
+
+    def counts(self) -> dict:
+        c = Counts()
+        lib.ccpm_result_counts(self.h, ctypes.byref(c))
+        return c.as_dict()
+
+    def phase_rounds(self):
+        c = self.counts()
+        out = np.zeros(max(c["n_phases"], 1), dtype=np.int32)
+        lib.ccpm_result_phase_rounds(self.h, _ptr(out)[0], int(c["n_phases"]))
+        return [int(x) for x in out[: c["n_phases"]]]
+
+    def close(self):
+        if self.h:
+            lib.ccpm_result_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prune(ctx: Context, graph: Graph, tmpl: Template, opts: Options | None = None,
+          result: Result | None = None, allow_budget: bool = False) -> Result:
+    """ccpm_prune; reuses `result` when given."""
+    h = ctypes.c_void_p(result.h.value if result is not None else None)
+    rc = lib.ccpm_prune(ctx.h, graph.h, tmpl.h, ctypes.byref(opts) if opts is not None else None,
+                        ctypes.byref(h))
+    if rc and not (rc == CCPM_EBUDGET and allow_budget):
+        if rc == CCPM_EBUDGET and h.value:
+            Result(graph, h).close() if result is None else None
+        ctx.check(rc, "ccpm_prune")
+    if result is not None:
+        return result
+    return Result(graph, h)

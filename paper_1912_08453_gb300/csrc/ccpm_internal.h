@@ -1,0 +1,78 @@
+// ccpm_internal.h -- structures shared by the host engine and the CUDA kernels.
+// Not part of the public ABI (see include/ccpm.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ccpm.h"
+
+namespace ccpm {
+
+constexpr int kMaxT = 32;           // template vertices (omega is one uint32)
+constexpr int kMaxCls = 32;         // label-multiplicity classes per template
+constexpr int kSmallDeg = 32;       // rows up to this length: 4 lanes per vertex
+constexpr int kDefaultHubDeg = 4096;// longer rows are split into chunks of this size
+constexpr uint64_t kDefaultSearchBudget = 1ull << 22;
+
+// Template tables for the LCC kernels.  A "class" is (q, L) with
+// |adj_L(q)| >= 2: vertex q of the template needs at least `need` distinct
+// active neighbours whose omega meets `mask` = adj_L(q) (Section 3.1 / 4.1).
+struct DevTmpl {
+    int n0;
+    int n_cls;
+    uint32_t adj[kMaxT];
+    uint32_t cls_mask[kMaxCls];
+    uint32_t cls_need[kMaxCls];
+    uint32_t cls_q[kMaxCls];
+};
+
+// Search plan of a rooted injective embedding of a substructure S: positions
+// 0..k-1, position 0 is the root.  Position i > 0 is found among the active
+// neighbours of position par[i]; back[i] lists earlier positions that must be
+// joined to it by an active edge; same[i] lists earlier positions whose
+// template vertex has the same label (injectivity only needs those).
+struct DevPlan {
+    int k;
+    int8_t q[kMaxT];
+    int8_t par[kMaxT];
+    uint32_t back[kMaxT];
+    uint32_t same[kMaxT];
+    // full-template enumeration marks these (position, position) edges
+    int n_marks;
+    int8_t mark_a[CCPM_MAX_TMPL_EDGES];
+    int8_t mark_b[CCPM_MAX_TMPL_EDGES];
+};
+
+struct HostConstraint {
+    int kind;
+    uint32_t vmask;
+    uint32_t hmask;
+    std::vector<std::pair<int, int>> edges;   // a < b, sorted
+    int gen_index;
+};
+
+struct Template {
+    int n0 = 0;
+    uint8_t labels[kMaxT] = {};
+    std::vector<std::pair<int, int>> edges;   // a < b, input order
+    uint32_t adj[kMaxT] = {};
+    std::vector<HostConstraint> k0;           // generated, fixed heuristic order
+    std::vector<int> order;                   // explicit order (indices into k0)
+    bool generated = false;
+    uint64_t automorphisms = 0;
+    std::string err;
+};
+
+// host helpers (ccpm_host.cpp)
+int  template_build(Template &t, int n0, const uint8_t *labels, int m0, const int32_t *edges);
+int  constraints_generate(Template &t, std::string &err);
+uint64_t count_automorphisms(const Template &t);
+void build_dev_tmpl(const Template &t, DevTmpl &d);
+// order[] of S's vertices from `root`: greedy, most back edges first, then
+// rarest background label, then lowest id.
+void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int root,
+                const int64_t *label_freq, bool with_marks, DevPlan &p);
+
+}  // namespace ccpm

@@ -1,0 +1,1428 @@
+// ccpm_kernels.cu -- sm_103a kernels of the constraint-checking pipeline and
+// the C ABI that drives them.
+//
+// Device state of one prune (the paper's vertex state, Alg. 3):
+//   omega[2][n]  uint32  omega(v) for rounds k and k+1 (snapshot/Jacobi LCC)
+//   ebits[W]     uint32  1 bit per CSR entry: the active edge map epsilon(v)
+// A vertex is active exactly when omega(v) != 0.
+//
+// Edge bits are kept exact for rows of active vertices only.  A bit in the row
+// of an active v that points to a vertex u eliminated in the previous round is
+// cleared lazily: the next round sees omega(u) = 0, treats the entry as
+// inactive and clears the bit.  Rows of eliminated vertices are zeroed when
+// they die; rows of vertices that never become active are zeroed only when
+// the edge bitmap is handed back without the final search.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ccpm_internal.h"
+
+namespace ccpm {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+// -------------------------------------------------------------------------
+// device-side bookkeeping
+// -------------------------------------------------------------------------
+
+struct RoundStats {
+    unsigned long long scanned;   // active CSR entries read this round
+    unsigned long long windows;   // CSR entries examined by searches
+    unsigned long long matches;   // final search: matches found
+    unsigned long long tokens;    // NLCC: (vertex, head) searches issued
+    unsigned long long row_entries;   // CSR entries in rows of active vertices
+    unsigned long long alive;         // active vertices processed
+    unsigned int changed;         // any omega or edge changed
+    unsigned int n_small, n_med, n_chunk;   // next frontier sizes
+    unsigned int n_hub_slots;
+    unsigned int n_roots;
+    unsigned int overflow;        // a search hit its budget
+    unsigned int pad;
+};
+
+struct HubAcc {                   // partial LCC state of one split row
+    uint32_t U, nN, flags, done;
+    uint32_t cnt[kMaxCls];
+};
+
+struct ChunkItem {                // one piece of a long row
+    int32_t v, c, slot, nchunks;
+};
+
+struct SmemTmpl {
+    uint32_t adj[kMaxT];
+    uint32_t cls_mask[kMaxCls];
+    uint32_t cls_need[kMaxCls];
+    uint32_t cls_q[kMaxCls];
+    int n_cls;
+};
+
+__device__ __forceinline__ void load_tmpl(SmemTmpl &s, const DevTmpl &t) {
+    for (int i = threadIdx.x; i < kMaxT; i += blockDim.x) s.adj[i] = t.adj[i];
+    for (int i = threadIdx.x; i < kMaxCls; i += blockDim.x) {
+        s.cls_mask[i] = t.cls_mask[i];
+        s.cls_need[i] = t.cls_need[i];
+        s.cls_q[i] = t.cls_q[i];
+    }
+    if (threadIdx.x == 0) s.n_cls = t.n_cls;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Per-warp staging buffer for frontier appends: one global atomic per 32 items.
+template <typename T>
+struct WarpBuf {
+    T *buf;          // 32 slots in shared memory
+    int *cnt;        // shared counter
+    T *out;          // global list
+    unsigned int *gcount;
+
+    __device__ __forceinline__ void flush() {
+        int c = *cnt;
+        if (c == 0) return;
+        unsigned int base = 0;
+        if (lane_id() == 0) base = atomicAdd(gcount, (unsigned int)c);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if ((int)lane_id() < c) out[base + lane_id()] = buf[lane_id()];
+        __syncwarp();
+        if (lane_id() == 0) *cnt = 0;
+        __syncwarp();
+    }
+    // warp-uniform call; lanes with pred push val
+    __device__ __forceinline__ void push(bool pred, const T &val) {
+        uint32_t m = __ballot_sync(FULL_MASK, pred);
+        if (!m) return;
+        int n = __popc(m);
+        if (*cnt + n > 32) flush();
+        int c = *cnt;
+        if (pred) buf[c + __popc(m & ((1u << lane_id()) - 1u))] = val;
+        __syncwarp();
+        if (lane_id() == 0) *cnt = c + n;
+        __syncwarp();
+    }
+};
+
+// Zero the bits of CSR entries [beg, end); `G` lanes cooperate.  Words fully
+// inside the range belong to this row alone and are stored; the two boundary
+// words are shared with neighbouring rows and are cleared atomically.
+template <int G>
+__device__ __forceinline__ void clear_row(uint32_t *ebits, int64_t beg, int64_t end, int lane_g) {
+    if (beg >= end) return;
+    int64_t w0 = beg >> 5, w1 = (end - 1) >> 5;
+    for (int64_t w = w0 + lane_g; w <= w1; w += G) {
+        int64_t lo = w << 5;
+        uint32_t keep = 0;
+        if (beg > lo) keep |= (1u << (uint32_t)(beg - lo)) - 1u;
+        if (end < lo + 32) keep |= ~((1u << (uint32_t)(end - lo)) - 1u);
+        if (keep) atomicAnd(&ebits[w], keep);
+        else ebits[w] = 0u;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t grp_or(uint32_t x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(FULL_MASK, x, o);
+    return x;
+}
+template <int G>
+__device__ __forceinline__ uint32_t grp_sum(uint32_t x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    return x;
+}
+
+// -------------------------------------------------------------------------
+// K1: INIT_VERTEX_STATE (Alg. 3) and the first frontier
+// -------------------------------------------------------------------------
+
+struct LabelMask { uint32_t m[256]; };
+
+__global__ void __launch_bounds__(256)
+k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ lab, LabelMask lm,
+       uint32_t *om0, uint32_t *om1, int32_t *small_out, int32_t *med_out, ChunkItem *chunk_out,
+       RoundStats *st, int hub_deg) {
+    __shared__ uint32_t slm[256];
+    __shared__ int32_t sbuf[2][8][32];
+    __shared__ int scnt[2][8];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) slm[i] = lm.m[i];
+    const int wib = threadIdx.x >> 5;
+    if (lane_id() == 0) { scnt[0][wib] = 0; scnt[1][wib] = 0; }
+    __syncthreads();
+    WarpBuf<int32_t> bs{sbuf[0][wib], &scnt[0][wib], small_out, &st->n_small};
+    WarpBuf<int32_t> bm{sbuf[1][wib], &scnt[1][wib], med_out, &st->n_med};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_pad = (n + 31) & ~(int64_t)31;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_pad; v += stride) {
+        uint32_t w = 0;
+        int64_t deg = 0;
+        if (v < n) {
+            w = slm[lab[v]];
+            om0[v] = w;
+            om1[v] = w;
+            if (w) deg = rp[v + 1] - rp[v];
+        }
+        // buckets: short rows (4 lanes each), medium rows (a warp each), long
+        // rows (split into pieces of hub_deg entries); every active vertex is
+        // in exactly one of them
+        const int64_t small_max = hub_deg < kSmallDeg ? hub_deg : kSmallDeg;
+        bs.push(w && deg <= small_max, (int32_t)v);
+        bm.push(w && deg > small_max && deg <= hub_deg, (int32_t)v);
+        if (w && deg > hub_deg) {
+            int nch = (int)((deg + hub_deg - 1) / hub_deg);
+            int slot = (int)atomicAdd(&st->n_hub_slots, 1u);
+            unsigned int base = atomicAdd(&st->n_chunk, (unsigned int)nch);
+            for (int c = 0; c < nch; c++) chunk_out[base + c] = ChunkItem{(int32_t)v, c, slot, nch};
+        }
+    }
+    bs.flush();
+    bm.flush();
+}
+
+// -------------------------------------------------------------------------
+// K2/K3: one LCC round (Alg. 4 with Alg. 5), snapshot form
+// -------------------------------------------------------------------------
+
+struct LccArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const uint32_t *om_cur;
+    uint32_t *om_next;
+    uint32_t *ebits;
+    const int32_t *small_in;
+    const int32_t *med_in;
+    const ChunkItem *chunk_in;
+    int64_t n_small, n_med, n_chunk;
+    int32_t *small_out;
+    int32_t *med_out;
+    ChunkItem *chunk_out;
+    HubAcc *acc;
+    RoundStats *st;
+    int hub_deg;
+};
+
+template <int MAXC>
+struct Partial {
+    uint32_t U = 0, nN = 0, achg = 0;
+    uint32_t cnt[MAXC > 0 ? MAXC : 1];
+    __device__ __forceinline__ Partial() {
+#pragma unroll
+        for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) cnt[c] = 0;
+    }
+};
+
+// Stream the CSR entries [beg, end) of an active vertex with G lanes: edge
+// elimination by eta (entry kept iff the neighbour's omega contains a template
+// neighbour of some q in omega(v)), the union omega' of Alg. 4 and the
+// per-class counts of distinct compatible neighbours.
+template <int G, int MAXC>
+__device__ __forceinline__ void scan_entries(int64_t beg, int64_t end, uint32_t nbr_v, int lane_g,
+                                             const int32_t *__restrict__ col,
+                                             const uint32_t *__restrict__ om, uint32_t *ebits,
+                                             const SmemTmpl &s, Partial<MAXC> &p,
+                                             unsigned long long &scanned) {
+    constexpr int UNR = 4;
+    for (int64_t base = beg + lane_g; base < end; base += (int64_t)G * UNR) {
+        uint32_t word[UNR];
+        int32_t u[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            int64_t e = base + (int64_t)j * G;
+            word[j] = 0u;
+            u[j] = 0;
+            if (e < end) {
+                word[j] = ebits[e >> 5];
+                u[j] = __ldg(col + e);
+            }
+        }
+        uint32_t wu[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            int64_t e = base + (int64_t)j * G;
+            bool act = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
+            wu[j] = act ? __ldg(om + u[j]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            uint32_t w = wu[j];
+            if (!w) continue;
+            scanned++;
+            if (w & nbr_v) {
+                p.U |= w;
+                p.nN++;
+#pragma unroll
+                for (int c = 0; c < MAXC; c++)
+                    if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
+            } else {
+                int64_t e = base + (int64_t)j * G;
+                atomicAnd(&ebits[e >> 5], ~(1u << (uint32_t)(e & 31)));
+                p.achg = 1u;
+            }
+        }
+    }
+}
+
+// The vertex-elimination rule of Alg. 4 plus the multiplicity rule of
+// Section 3.1: q survives iff adj(q) is inside omega' and every class of q
+// has enough distinct neighbours; no surviving edge eliminates the vertex.
+template <int MAXC>
+__device__ __forceinline__ uint32_t decide(uint32_t wv, const Partial<MAXC> &p, const SmemTmpl &s) {
+    uint32_t keep = 0;
+    for (uint32_t m = wv; m; m &= m - 1u) {
+        int q = __ffs(m) - 1;
+        if ((s.adj[q] & ~p.U) == 0u) keep |= 1u << q;
+    }
+#pragma unroll
+    for (int c = 0; c < MAXC; c++)
+        if (c < s.n_cls && p.cnt[c] < s.cls_need[c]) keep &= ~(1u << s.cls_q[c]);
+    if (p.nN == 0u) keep = 0u;
+    return keep;
+}
+
+__device__ __forceinline__ uint32_t nbr_mask(uint32_t wv, const SmemTmpl &s) {
+    uint32_t m = 0;
+    for (uint32_t x = wv; x; x &= x - 1u) m |= s.adj[__ffs(x) - 1];
+    return m;
+}
+
+template <int MAXC>
+__global__ void __launch_bounds__(256)
+k_lcc_round(LccArgs a, DevTmpl t) {
+    __shared__ SmemTmpl s;
+    __shared__ int32_t sbuf[2][8][32];
+    __shared__ ChunkItem cbuf[8][32];
+    __shared__ int scnt[3][8];
+    load_tmpl(s, t);
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    if (lane == 0) { scnt[0][wib] = 0; scnt[1][wib] = 0; scnt[2][wib] = 0; }
+    __syncthreads();
+    WarpBuf<int32_t> bs{sbuf[0][wib], &scnt[0][wib], a.small_out, &a.st->n_small};
+    WarpBuf<int32_t> bm{sbuf[1][wib], &scnt[1][wib], a.med_out, &a.st->n_med};
+    WarpBuf<ChunkItem> bc{cbuf[wib], &scnt[2][wib], a.chunk_out, &a.st->n_chunk};
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long scanned = 0, rows = 0, alive = 0;
+    uint32_t changed = 0;
+
+    // (1) pieces of long rows: one warp per piece, combined through HubAcc;
+    // the last piece to finish decides for the vertex.
+    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+        ChunkItem ci = a.chunk_in[it];
+        const uint32_t wv = __ldg(a.om_cur + ci.v);
+        if (wv == 0u) {
+            if (ci.c == 0 && lane == 0) a.om_next[ci.v] = 0u;
+            continue;
+        }
+        const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
+        const int64_t beg = rbeg + (int64_t)ci.c * a.hub_deg;
+        const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
+        if (lane == 0) { rows += (unsigned long long)(end - beg); alive += ci.c == 0; }
+        Partial<MAXC> p;
+        scan_entries<32, MAXC>(beg, end, nbr_mask(wv, s), lane, a.col, a.om_cur, a.ebits, s, p, scanned);
+        p.U = grp_or<32>(p.U);
+        p.nN = grp_sum<32>(p.nN);
+        p.achg = grp_or<32>(p.achg);
+#pragma unroll
+        for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
+        HubAcc *h = a.acc + ci.slot;
+        unsigned int ticket = 0;
+        if (lane == 0) {
+            if (p.U) atomicOr(&h->U, p.U);
+            if (p.nN) atomicAdd(&h->nN, p.nN);
+            if (p.achg) atomicOr(&h->flags, 1u);
+#pragma unroll
+            for (int c = 0; c < MAXC; c++)
+                if (p.cnt[c]) atomicAdd(&h->cnt[c], p.cnt[c]);
+            __threadfence();
+            ticket = atomicAdd(&h->done, 1u);
+        }
+        ticket = __shfl_sync(FULL_MASK, ticket, 0);
+        if (ticket == (unsigned int)(ci.nchunks - 1)) {
+            __threadfence();
+            Partial<MAXC> tot;
+            tot.U = atomicOr(&h->U, 0u);
+            tot.nN = atomicAdd(&h->nN, 0u);
+            tot.achg = atomicOr(&h->flags, 0u);
+#pragma unroll
+            for (int c = 0; c < MAXC; c++) tot.cnt[c] = atomicAdd(&h->cnt[c], 0u);
+            uint32_t keep = decide<MAXC>(wv, tot, s);
+            if (lane == 0) a.om_next[ci.v] = keep;
+            if (keep != wv || tot.achg) changed = 1u;
+            if (keep == 0u) clear_row<32>(a.ebits, rbeg, rend, lane);
+            __syncwarp();
+            if (lane == 0) {
+                h->U = 0u; h->nN = 0u; h->flags = 0u; h->done = 0u;
+                for (int c = 0; c < MAXC; c++) h->cnt[c] = 0u;
+            }
+        }
+        bc.push(lane == 0, ci);
+    }
+
+    // (2) medium rows: one warp per vertex
+    for (int64_t it = gwarp; it < a.n_med; it += nwarps) {
+        const int32_t v = a.med_in[it];
+        const uint32_t wv = __ldg(a.om_cur + v);
+        uint32_t keep = 0u;
+        if (wv) {
+            const int64_t beg = a.rp[v], end = a.rp[v + 1];
+            if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
+            Partial<MAXC> p;
+            scan_entries<32, MAXC>(beg, end, nbr_mask(wv, s), lane, a.col, a.om_cur, a.ebits, s, p, scanned);
+            p.U = grp_or<32>(p.U);
+            p.nN = grp_sum<32>(p.nN);
+            p.achg = grp_or<32>(p.achg);
+#pragma unroll
+            for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
+            keep = decide<MAXC>(wv, p, s);
+            if (keep != wv || p.achg) changed = 1u;
+            if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
+        }
+        if (lane == 0) a.om_next[v] = keep;
+        bm.push(lane == 0 && wv != 0u, v);
+    }
+
+    // (3) short rows: 4 lanes per vertex, 8 vertices per warp step
+    const int g = lane >> 2, lg = lane & 3;
+    const int64_t n_steps = (a.n_small + 7) / 8;
+    for (int64_t it = gwarp; it < n_steps; it += nwarps) {
+        const int64_t idx = it * 8 + g;
+        const int32_t v = idx < a.n_small ? a.small_in[idx] : -1;
+        const uint32_t wv = v >= 0 ? __ldg(a.om_cur + v) : 0u;
+        int64_t beg = 0, end = 0;
+        if (wv) { beg = a.rp[v]; end = a.rp[v + 1]; }
+        if (lg == 0 && wv) { rows += (unsigned long long)(end - beg); alive++; }
+        Partial<MAXC> p;
+        scan_entries<4, MAXC>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits, s, p, scanned);
+        p.U = grp_or<4>(p.U);
+        p.nN = grp_sum<4>(p.nN);
+        p.achg = grp_or<4>(p.achg);
+#pragma unroll
+        for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<4>(p.cnt[c]);
+        uint32_t keep = wv ? decide<MAXC>(wv, p, s) : 0u;
+        if (wv && (keep != wv || p.achg)) changed = 1u;
+        if (wv && keep == 0u) clear_row<4>(a.ebits, beg, end, lg);
+        if (v >= 0 && lg == 0) a.om_next[v] = keep;
+        bs.push(lg == 0 && wv != 0u, v);
+    }
+
+    bs.flush();
+    bm.flush();
+    bc.flush();
+    // warp totals
+    for (int o = 16; o > 0; o >>= 1) {
+        scanned += __shfl_xor_sync(FULL_MASK, scanned, o);
+        rows += __shfl_xor_sync(FULL_MASK, rows, o);
+        alive += __shfl_xor_sync(FULL_MASK, alive, o);
+        changed |= __shfl_xor_sync(FULL_MASK, changed, o);
+    }
+    if (lane == 0) {
+        if (scanned) atomicAdd(&a.st->scanned, scanned);
+        if (rows) atomicAdd(&a.st->row_entries, rows);
+        if (alive) atomicAdd(&a.st->alive, alive);
+        if (changed) atomicOr(&a.st->changed, 1u);
+    }
+}
+
+// -------------------------------------------------------------------------
+// Rooted injective embedding search (NLCC token walk, Alg. 6/7, and the
+// final template-driven search, Remark 1).  One warp per root vertex; the
+// warp walks the plan depth first, testing 32 neighbours of the anchor at a
+// time in parallel.
+// -------------------------------------------------------------------------
+
+struct SearchArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const uint32_t *om;
+    const uint32_t *ebits;
+    const int32_t *roots;
+    int64_t n_roots;
+    const DevPlan *plans;     // plans[h] for each head h (NLCC) or plans[0] (final)
+    uint32_t heads;           // NLCC: heads of the constraint; final: 1 << plans[0].q[0]
+    uint32_t *sat;            // NLCC output: satisfied heads per vertex
+    uint32_t *om_out;         // final: omega*
+    uint32_t *eb_out;         // final: edge bitmap of E*
+    RoundStats *st;
+    uint64_t budget;          // windows per (root, head)
+    uint64_t cap;             // final: stop past this many matches
+};
+
+struct WarpSearch {
+    int32_t psi[kMaxT];
+    int32_t cand[kMaxT][32];
+    int64_t pos[kMaxT];
+    int64_t end[kMaxT];
+    uint32_t mask[kMaxT];
+};
+
+__device__ __forceinline__ bool ebit(const uint32_t *eb, int64_t e) {
+    return (eb[e >> 5] >> (uint32_t)(e & 31)) & 1u;
+}
+
+// CSR entry index of (x, y) or -1: binary search over the sorted row of x.
+__device__ __forceinline__ int64_t find_entry(const int64_t *rp, const int32_t *col, int32_t x, int32_t y) {
+    int64_t lo = rp[x], hi = rp[x + 1];
+    const int64_t stop = hi;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(col + mid) < y) lo = mid + 1; else hi = mid;
+    }
+    return (lo < stop && __ldg(col + lo) == y) ? lo : -1;
+}
+
+// Active edge between x and y?  Searches the shorter of the two rows.
+__device__ __forceinline__ bool edge_active(const int64_t *rp, const int32_t *col, const uint32_t *eb,
+                                            int32_t x, int32_t y) {
+    int64_t dx = rp[x + 1] - rp[x], dy = rp[y + 1] - rp[y];
+    int64_t e = dx <= dy ? find_entry(rp, col, x, y) : find_entry(rp, col, y, x);
+    return e >= 0 && ebit(eb, e);
+}
+
+// Returns true if an embedding exists (ENUM = false) / after enumerating all
+// embeddings from this root (ENUM = true).  *over is set when the window
+// budget ran out; for existence the root is then reported as satisfied, which
+// keeps the result a superset of the exact answer.
+template <bool ENUM>
+__device__ bool search_root(const SearchArgs &a, const DevPlan &P, int32_t root, WarpSearch &W,
+                            unsigned long long &windows, unsigned long long &matches, bool &over) {
+    const int lane = (int)lane_id();
+    const int k = P.k;
+    uint64_t used = 0;
+    if (lane == 0) {
+        W.psi[0] = root;
+        int32_t anchor = root;
+        W.pos[1] = a.rp[anchor];
+        W.end[1] = a.rp[anchor + 1];
+        W.mask[1] = 0u;
+    }
+    __syncwarp();
+    int d = 1;
+    while (d >= 1) {
+        uint32_t m = W.mask[d];
+        if (m == 0u) {
+            const int64_t pos = W.pos[d], end = W.end[d];
+            if (pos >= end) { d--; continue; }
+            if (++used > a.budget) { over = true; return !ENUM; }
+            windows += (unsigned long long)min((int64_t)32, end - pos);
+            const int64_t e = pos + lane;
+            const int q = P.q[d];
+            bool ok = false;
+            int32_t u = -1;
+            if (e < end && ebit(a.ebits, e)) {
+                u = __ldg(a.col + e);
+                if ((__ldg(a.om + u) >> q) & 1u) {
+                    ok = true;
+                    for (uint32_t sm = P.same[d]; sm && ok; sm &= sm - 1u)
+                        if (W.psi[__ffs(sm) - 1] == u) ok = false;
+                    for (uint32_t bm = P.back[d]; bm && ok; bm &= bm - 1u)
+                        ok = edge_active(a.rp, a.col, a.ebits, W.psi[__ffs(bm) - 1], u);
+                }
+            }
+            const uint32_t vm = __ballot_sync(FULL_MASK, ok);
+            W.cand[d][lane] = u;
+            __syncwarp();
+            if (lane == 0) { W.mask[d] = vm; W.pos[d] = pos + 32; }
+            __syncwarp();
+            continue;
+        }
+        const int b = __ffs(m) - 1;
+        if (lane == 0) { W.mask[d] = m & (m - 1u); W.psi[d] = W.cand[d][b]; }
+        __syncwarp();
+        if (d == k - 1) {
+            if (!ENUM) return true;
+            matches++;
+            // mark the match: omega*(psi(i)) gets q_i, both directions of
+            // every template edge get their bit
+            if (lane < k) {
+                int32_t x = W.psi[lane];
+                uint32_t bit = 1u << P.q[lane];
+                if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
+            }
+            for (int t = lane; t < P.n_marks; t += 32) {
+                int32_t x = W.psi[P.mark_a[t]], y = W.psi[P.mark_b[t]];
+                int64_t e1 = find_entry(a.rp, a.col, x, y);
+                int64_t e2 = find_entry(a.rp, a.col, y, x);
+                if (e1 >= 0) {
+                    uint32_t b1 = 1u << (uint32_t)(e1 & 31);
+                    if (!(a.eb_out[e1 >> 5] & b1)) atomicOr(&a.eb_out[e1 >> 5], b1);
+                }
+                if (e2 >= 0) {
+                    uint32_t b2 = 1u << (uint32_t)(e2 & 31);
+                    if (!(a.eb_out[e2 >> 5] & b2)) atomicOr(&a.eb_out[e2 >> 5], b2);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        d++;
+        if (lane == 0) {
+            int32_t anchor = W.psi[P.par[d]];
+            W.pos[d] = a.rp[anchor];
+            W.end[d] = a.rp[anchor + 1];
+            W.mask[d] = 0u;
+        }
+        __syncwarp();
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(128)
+k_nlcc_search(SearchArgs a) {
+    __shared__ WarpSearch ws[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long windows = 0, matches = 0, tokens = 0;
+    bool over = false;
+    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+        const int32_t v = a.roots[it];
+        const uint32_t hv = __ldg(a.om + v) & a.heads;
+        tokens += (unsigned long long)__popc(hv);
+        uint32_t sat = 0;
+        for (uint32_t hm = hv; hm; hm &= hm - 1u) {
+            const int h = __ffs(hm) - 1;
+            if (search_root<false>(a, a.plans[h], v, W, windows, matches, over)) sat |= 1u << h;
+            __syncwarp();
+        }
+        if (lane == 0) a.sat[v] = sat;
+    }
+    for (int o = 16; o > 0; o >>= 1) windows += __shfl_xor_sync(FULL_MASK, windows, o);
+    uint32_t ov = __ballot_sync(FULL_MASK, over);
+    if (lane == 0) {
+        if (windows) atomicAdd(&a.st->windows, windows);
+        if (tokens) atomicAdd(&a.st->tokens, tokens);
+        if (ov) atomicOr(&a.st->overflow, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(128)
+k_final_search(SearchArgs a) {
+    __shared__ WarpSearch ws[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long windows = 0, matches = 0;
+    bool over = false;
+    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+        unsigned int stop = 0;
+        if (lane == 0) stop = *(volatile unsigned int *)&a.st->overflow;
+        if (__shfl_sync(FULL_MASK, stop, 0)) break;
+        const int32_t v = a.roots[it];
+        unsigned long long before = matches;
+        search_root<true>(a, a.plans[0], v, W, windows, matches, over);
+        __syncwarp();
+        if (matches != before) {
+            unsigned long long tot = 0;
+            if (lane == 0) tot = atomicAdd(&a.st->matches, matches - before) + (matches - before);
+            tot = __shfl_sync(FULL_MASK, tot, 0);
+            if (tot > a.cap) over = true;
+        }
+        if (over) {
+            if (lane == 0) atomicOr(&a.st->overflow, 1u);
+            break;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) windows += __shfl_xor_sync(FULL_MASK, windows, o);
+    if (lane == 0 && windows) atomicAdd(&a.st->windows, windows);
+}
+
+// Roots of a search: every vertex whose omega meets `heads`.
+__global__ void __launch_bounds__(256)
+k_collect_roots(int64_t n, const uint32_t *__restrict__ om, uint32_t heads, int32_t *roots, RoundStats *st) {
+    __shared__ int32_t sbuf[8][32];
+    __shared__ int scnt[8];
+    const int wib = threadIdx.x >> 5;
+    if (lane_id() == 0) scnt[wib] = 0;
+    __syncthreads();
+    WarpBuf<int32_t> b{sbuf[wib], &scnt[wib], roots, &st->n_roots};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_pad = (n + 31) & ~(int64_t)31;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_pad; v += stride) {
+        bool p = v < n && (__ldg(om + v) & heads);
+        b.push(p, (int32_t)v);
+    }
+    b.flush();
+}
+
+// Alg. 6 lines 5-11: issuers whose token failed lose the head; a vertex whose
+// omega empties is eliminated with its edges.  Both omega buffers are kept
+// equal (they are equal at an LCC fixpoint).
+__global__ void __launch_bounds__(256)
+k_nlcc_apply(const int32_t *__restrict__ roots, int64_t n_roots, uint32_t heads,
+             const uint32_t *__restrict__ sat, uint32_t *om0, uint32_t *om1,
+             const int64_t *__restrict__ rp, uint32_t *ebits, RoundStats *st) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t changed = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_roots; i += stride) {
+        const int32_t v = roots[i];
+        const uint32_t w = om0[v];
+        const uint32_t nw = w & ~(heads & ~sat[v]);
+        if (nw != w) {
+            om0[v] = nw;
+            om1[v] = nw;
+            changed = 1u;
+            if (nw == 0u) clear_row<1>(ebits, rp[v], rp[v + 1], 0);
+        }
+    }
+    if (__any_sync(FULL_MASK, changed) && lane_id() == 0) atomicOr(&st->changed, 1u);
+}
+
+// Make the edge map exact everywhere (used when it is handed back without the
+// final search): rows of inactive vertices are zeroed, and in live rows the
+// bits of entries whose other end is inactive are cleared.  One warp per vertex.
+__global__ void __launch_bounds__(256)
+k_materialize(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ col, uint32_t *ebits) {
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t v = gwarp; v < n; v += nwarps) {
+        const int64_t beg = rp[v], end = rp[v + 1];
+        if (beg == end) continue;
+        if (om[v] == 0u) {
+            clear_row<32>(ebits, beg, end, lane);
+            continue;
+        }
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            if (ebit(ebits, e) && om[col[e]] == 0u)
+                atomicAnd(&ebits[e >> 5], ~(1u << (uint32_t)(e & 31)));
+        }
+    }
+}
+
+__global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
+
+// Population counts for the result summary.
+__global__ void __launch_bounds__(256)
+k_count(int64_t n, const uint32_t *__restrict__ om, int64_t words, const uint32_t *__restrict__ eb,
+        unsigned long long *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long av = 0, ae = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) av += om[i] != 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) ae += __popc(eb[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        av += __shfl_xor_sync(FULL_MASK, av, o);
+        ae += __shfl_xor_sync(FULL_MASK, ae, o);
+    }
+    if (lane_id() == 0) {
+        if (av) atomicAdd(&out[0], av);
+        if (ae) atomicAdd(&out[1], ae);
+    }
+}
+
+}  // namespace ccpm
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+using namespace ccpm;
+
+struct ccpm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string err;
+};
+
+struct Workspace {
+    int64_t n = 0, m = 0, words = 0;
+    int hub_deg = 0;
+    uint32_t *om[2] = {nullptr, nullptr};
+    uint32_t *ebits = nullptr;
+    int32_t *small[2] = {nullptr, nullptr};
+    int32_t *med[2] = {nullptr, nullptr};
+    ChunkItem *chunk[2] = {nullptr, nullptr};
+    int64_t chunk_cap = 0;
+    HubAcc *acc = nullptr;
+    int64_t acc_cap = 0;
+    int32_t *roots = nullptr;
+    uint32_t *sat = nullptr;
+    DevPlan *plans = nullptr;
+    RoundStats *st = nullptr;        // device
+    RoundStats *st_h = nullptr;      // pinned host mirror
+    unsigned long long *cnt = nullptr;
+    unsigned long long *cnt_h = nullptr;
+    DevPlan *plans_h = nullptr;      // pinned staging for plan uploads
+    cudaEvent_t ev[8] = {};
+};
+
+struct ccpm_graph {
+    ccpm_ctx *ctx = nullptr;
+    int64_t n = 0, m = 0;
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    uint8_t *lab = nullptr;
+    bool borrowed = false;
+    int64_t label_freq[256] = {};
+    Workspace ws;
+};
+
+struct ccpm_tmpl {
+    ccpm_ctx *ctx = nullptr;
+    Template t;
+};
+
+struct ccpm_result {
+    ccpm_graph *g = nullptr;
+    uint32_t *om = nullptr;
+    uint32_t *eb = nullptr;
+    ccpm_counts counts{};
+    std::vector<int32_t> phase_rounds;
+};
+
+namespace {
+
+int set_err(ccpm_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+#define CU(ctx, call)                                                                 \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return set_err((ctx), e_ == cudaErrorMemoryAllocation ? CCPM_ENOMEM : CCPM_ECUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+template <typename T>
+int dalloc(ccpm_ctx *ctx, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return set_err(ctx, CCPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return CCPM_OK;
+}
+
+void ws_free(Workspace &w) {
+    cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.ebits);
+    cudaFree(w.small[0]); cudaFree(w.small[1]); cudaFree(w.med[0]); cudaFree(w.med[1]);
+    cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
+    cudaFree(w.sat); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt);
+    if (w.st_h) cudaFreeHost(w.st_h);
+    if (w.cnt_h) cudaFreeHost(w.cnt_h);
+    if (w.plans_h) cudaFreeHost(w.plans_h);
+    for (auto &e : w.ev) if (e) cudaEventDestroy(e);
+    w = Workspace{};
+}
+
+int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
+    Workspace &w = g->ws;
+    if (w.om[0] && w.hub_deg == hub_deg) return CCPM_OK;
+    ws_free(w);
+    w.n = g->n;
+    w.m = g->m;
+    w.words = (g->m + 31) / 32;
+    w.hub_deg = hub_deg;
+    w.chunk_cap = 2 * (g->m / hub_deg) + 16;
+    w.acc_cap = g->m / hub_deg + 16;
+    int rc;
+    if ((rc = dalloc(ctx, &w.om[0], (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.om[1], (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.ebits, (size_t)w.words + 1))) return rc;
+    for (int i = 0; i < 2; i++) {
+        if ((rc = dalloc(ctx, &w.small[i], (size_t)g->n))) return rc;
+        if ((rc = dalloc(ctx, &w.med[i], (size_t)g->n))) return rc;
+        if ((rc = dalloc(ctx, &w.chunk[i], (size_t)w.chunk_cap))) return rc;
+    }
+    if ((rc = dalloc(ctx, &w.acc, (size_t)w.acc_cap))) return rc;
+    if ((rc = dalloc(ctx, &w.roots, (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.sat, (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxT))) return rc;
+    if ((rc = dalloc(ctx, &w.st, 1))) return rc;
+    if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
+    CU(ctx, cudaMallocHost((void **)&w.st_h, sizeof(RoundStats)));
+    CU(ctx, cudaMallocHost((void **)&w.cnt_h, 2 * sizeof(unsigned long long)));
+    CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxT * sizeof(DevPlan)));
+    CU(ctx, cudaMemsetAsync(w.acc, 0, sizeof(HubAcc) * (size_t)w.acc_cap, ctx->stream));
+    for (auto &e : w.ev) CU(ctx, cudaEventCreate(&e));
+    return CCPM_OK;
+}
+
+int grid_for(ccpm_ctx *ctx, int64_t work_items, int per_block, int blocks_per_sm) {
+    int64_t need = (work_items + per_block - 1) / per_block;
+    int64_t cap = (int64_t)ctx->num_sms * blocks_per_sm;
+    if (need < 1) need = 1;
+    return (int)std::min(need, cap);
+}
+
+struct Pipeline {
+    ccpm_ctx *ctx;
+    ccpm_graph *g;
+    const Template *t;
+    DevTmpl dt;
+    int cur = 0;            // omega buffer holding round-k state
+    int li = 0;             // frontier list parity
+    int64_t n_small = 0, n_med = 0, n_chunk = 0;
+    int64_t scanned = 0;
+    int64_t windows = 0;
+    int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
+    double ms_lcc_kernel = 0.0;
+    int maxc = 0;
+
+    int read_stats() {
+        Workspace &w = g->ws;
+        CU(ctx, cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return CCPM_OK;
+    }
+
+    int launch_round() {
+        Workspace &w = g->ws;
+        LccArgs a;
+        a.rp = g->rp;
+        a.col = g->col;
+        a.om_cur = w.om[cur];
+        a.om_next = w.om[cur ^ 1];
+        a.ebits = w.ebits;
+        a.small_in = w.small[li];
+        a.med_in = w.med[li];
+        a.chunk_in = w.chunk[li];
+        a.n_small = n_small;
+        a.n_med = n_med;
+        a.n_chunk = n_chunk;
+        a.small_out = w.small[li ^ 1];
+        a.med_out = w.med[li ^ 1];
+        a.chunk_out = w.chunk[li ^ 1];
+        a.acc = w.acc;
+        a.st = w.st;
+        a.hub_deg = w.hub_deg;
+        int64_t warps = n_chunk + n_med + (n_small + 7) / 8;
+        int grid = grid_for(ctx, warps * 32, 256, 8);
+        launches++;
+        lcc_launches++;
+        if (maxc == 0) k_lcc_round<0><<<grid, 256, 0, ctx->stream>>>(a, dt);
+        else if (maxc <= 4) k_lcc_round<4><<<grid, 256, 0, ctx->stream>>>(a, dt);
+        else k_lcc_round<32><<<grid, 256, 0, ctx->stream>>>(a, dt);
+        CU(ctx, cudaGetLastError());
+        return CCPM_OK;
+    }
+
+    // LCC to fixpoint; returns rounds via *rounds.
+    int lcc(int64_t *rounds) {
+        Workspace &w = g->ws;
+        int64_t r = 0;
+        for (;;) {
+            CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), ctx->stream));
+            CU(ctx, cudaEventRecord(w.ev[4], ctx->stream));
+            int rc = launch_round();
+            if (rc) return rc;
+            CU(ctx, cudaEventRecord(w.ev[5], ctx->stream));
+            if ((rc = read_stats())) return rc;
+            float ms = 0.f;
+            CU(ctx, cudaEventElapsedTime(&ms, w.ev[4], w.ev[5]));
+            ms_lcc_kernel += ms;
+            r++;
+            scanned += (int64_t)w.st_h->scanned;
+            rows += (int64_t)w.st_h->row_entries;
+            alive += (int64_t)w.st_h->alive;
+            n_small = w.st_h->n_small;
+            n_med = w.st_h->n_med;
+            n_chunk = w.st_h->n_chunk;
+            li ^= 1;
+            cur ^= 1;
+            if (!w.st_h->changed) break;
+            if (r > (int64_t)4 * (g->m + g->n) + 8)
+                return set_err(ctx, CCPM_ETIMEOUT, "LCC did not converge");
+        }
+        *rounds = r;
+        return CCPM_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void ccpm_options_default(ccpm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->order_mode = CCPM_ORDER_FIXED;
+    o->run_final = 1;
+    o->max_embeddings = 1ull << 32;
+    o->search_budget = 0;
+    o->hub_degree = 0;
+}
+
+int ccpm_ctx_create(int device, void *stream, ccpm_ctx_t *out) {
+    if (!out) return CCPM_EINVAL;
+    *out = nullptr;
+    ccpm_ctx *c = new (std::nothrow) ccpm_ctx();
+    if (!c) return CCPM_ENOMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        delete c;
+        return CCPM_ECUDA;
+    }
+    *out = c;
+    return CCPM_OK;
+}
+
+void ccpm_ctx_destroy(ccpm_ctx_t c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *ccpm_last_error(ccpm_ctx_t c) { return c ? c->err.c_str() : "null context"; }
+
+int ccpm_graph_load_csr(ccpm_ctx_t ctx, int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                        const uint8_t *labels, int flags, ccpm_graph_t *out) {
+    if (!ctx || !out) return CCPM_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t)1 << 31 || m < 0 || !row_ptr || !labels || (m > 0 && !col))
+        return set_err(ctx, CCPM_EINVAL, "graph: need 1 <= n < 2^31, m >= 0 and non-NULL arrays");
+    CU(ctx, cudaSetDevice(ctx->device));
+    const bool dev = (flags & CCPM_DEVICE_PTRS) != 0;
+    if (!dev) {
+        if (row_ptr[0] != 0 || row_ptr[n] != m)
+            return set_err(ctx, CCPM_EINVAL, "graph: row_ptr[0] must be 0 and row_ptr[n] == m_dir");
+        for (int64_t v = 0; v < n; v++)
+            if (row_ptr[v + 1] < row_ptr[v]) return set_err(ctx, CCPM_EINVAL, "graph: row_ptr not monotone");
+        if (flags & CCPM_VALIDATE) {
+            for (int64_t v = 0; v < n; v++) {
+                for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+                    int32_t u = col[e];
+                    if (u < 0 || u >= n) return set_err(ctx, CCPM_EINVAL, "graph: column index out of range");
+                    if (u == v) return set_err(ctx, CCPM_EINVAL, "graph: self loop");
+                    if (e > row_ptr[v] && col[e - 1] >= u)
+                        return set_err(ctx, CCPM_EINVAL, "graph: row not sorted or duplicate entry");
+                    // reverse entry must exist
+                    const int32_t *lo = col + row_ptr[u], *hi = col + row_ptr[u + 1];
+                    const int32_t *f = std::lower_bound(lo, hi, (int32_t)v);
+                    if (f == hi || *f != v) return set_err(ctx, CCPM_EINVAL, "graph: missing reverse entry");
+                }
+            }
+        }
+    } else if (flags & CCPM_VALIDATE) {
+        return set_err(ctx, CCPM_EINVAL, "graph: CCPM_VALIDATE needs host pointers");
+    }
+    ccpm_graph *g = new (std::nothrow) ccpm_graph();
+    if (!g) return set_err(ctx, CCPM_ENOMEM, "graph: host allocation");
+    g->ctx = ctx;
+    g->n = n;
+    g->m = m;
+    g->borrowed = dev;
+    if (dev) {
+        g->rp = const_cast<int64_t *>(row_ptr);
+        g->col = const_cast<int32_t *>(col);
+        g->lab = const_cast<uint8_t *>(labels);
+        std::vector<uint8_t> h((size_t)n);
+        cudaError_t e = cudaMemcpy(h.data(), labels, (size_t)n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { delete g; return set_err(ctx, CCPM_ECUDA, "graph: label readback"); }
+        for (int64_t v = 0; v < n; v++) g->label_freq[h[v]]++;
+    } else {
+        int rc;
+        if ((rc = dalloc(ctx, &g->rp, (size_t)n + 1)) || (rc = dalloc(ctx, &g->col, (size_t)m)) ||
+            (rc = dalloc(ctx, &g->lab, (size_t)n))) {
+            cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab);
+            delete g;
+            return rc;
+        }
+        cudaError_t e = cudaMemcpyAsync(g->rp, row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync(g->col, col, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->lab, labels, (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab);
+            delete g;
+            return set_err(ctx, CCPM_ECUDA, std::string("graph upload: ") + cudaGetErrorString(e));
+        }
+        for (int64_t v = 0; v < n; v++) g->label_freq[labels[v]]++;
+    }
+    *out = g;
+    return CCPM_OK;
+}
+
+void ccpm_graph_destroy(ccpm_graph_t g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    ws_free(g->ws);
+    if (!g->borrowed) { cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab); }
+    delete g;
+}
+
+int ccpm_tmpl_load(ccpm_ctx_t ctx, int n0, const uint8_t *labels, int m0, const int32_t *edges, ccpm_tmpl_t *out) {
+    if (!out) return CCPM_EINVAL;
+    *out = nullptr;
+    ccpm_tmpl *t = new (std::nothrow) ccpm_tmpl();
+    if (!t) return CCPM_ENOMEM;
+    t->ctx = ctx;
+    int rc = template_build(t->t, n0, labels, m0, edges);
+    if (rc) {
+        if (ctx) ctx->err = t->t.err;
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return CCPM_OK;
+}
+
+void ccpm_tmpl_destroy(ccpm_tmpl_t t) { delete t; }
+
+int ccpm_constraints_generate(ccpm_tmpl_t t, ccpm_graph_t g, int *n) {
+    (void)g;
+    if (!t) return CCPM_EINVAL;
+    std::string err;
+    int rc = constraints_generate(t->t, err);
+    if (rc) {
+        t->t.err = err;
+        if (t->ctx) t->ctx->err = err;
+        return rc;
+    }
+    if (n) *n = (int)t->t.k0.size();
+    return CCPM_OK;
+}
+
+int ccpm_constraints_describe(ccpm_tmpl_t t, int i, ccpm_constraint_info *out) {
+    if (!t || !out || !t->t.generated) return CCPM_ESTATE;
+    if (i < 0 || i >= (int)t->t.order.size()) return CCPM_EINVAL;
+    const HostConstraint &c = t->t.k0[(size_t)t->t.order[(size_t)i]];
+    std::memset(out, 0, sizeof(*out));
+    out->kind = c.kind;
+    out->vert_mask = c.vmask;
+    out->head_mask = c.hmask;
+    out->n_verts = __builtin_popcount(c.vmask);
+    out->n_edges = (int)c.edges.size();
+    for (size_t k = 0; k < c.edges.size(); k++) {
+        out->edges[k][0] = c.edges[k].first;
+        out->edges[k][1] = c.edges[k].second;
+    }
+    return CCPM_OK;
+}
+
+int ccpm_tmpl_set_order(ccpm_tmpl_t t, int n, const int32_t *order) {
+    if (!t || !t->t.generated) return CCPM_ESTATE;
+    if (n != (int)t->t.k0.size() || (n > 0 && !order)) return CCPM_EINVAL;
+    std::vector<int> seen((size_t)n, 0), ord((size_t)n);
+    for (int i = 0; i < n; i++) {
+        if (order[i] < 0 || order[i] >= n || seen[(size_t)order[i]]) return CCPM_EINVAL;
+        seen[(size_t)order[i]] = 1;
+        ord[(size_t)i] = order[i];
+    }
+    t->t.order = ord;
+    return CCPM_OK;
+}
+
+int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_options *opt_in, ccpm_result_t *out) {
+    if (!ctx || !g || !tm || !out) return CCPM_EINVAL;
+    if (g->ctx != ctx) return set_err(ctx, CCPM_EINVAL, "graph belongs to another context");
+    ccpm_options opt;
+    if (opt_in) opt = *opt_in; else ccpm_options_default(&opt);
+    CU(ctx, cudaSetDevice(ctx->device));
+    Template &t = tm->t;
+    if (!t.generated) {
+        std::string err;
+        int rc = constraints_generate(t, err);
+        if (rc) return set_err(ctx, rc, err);
+    }
+    const int hub_deg = opt.hub_degree > 0 ? opt.hub_degree : kDefaultHubDeg;
+    const uint64_t budget = opt.search_budget ? opt.search_budget : kDefaultSearchBudget;
+    int rc = ws_ensure(ctx, g, hub_deg);
+    if (rc) return rc;
+    Workspace &w = g->ws;
+    ccpm_result *r = *out;
+    if (r && r->g != g) return set_err(ctx, CCPM_EINVAL, "result was made for another graph");
+    bool fresh = false;
+    if (!r) {
+        r = new (std::nothrow) ccpm_result();
+        if (!r) return set_err(ctx, CCPM_ENOMEM, "result: host allocation");
+        r->g = g;
+        if ((rc = dalloc(ctx, &r->om, (size_t)g->n)) || (rc = dalloc(ctx, &r->eb, (size_t)w.words + 1))) {
+            cudaFree(r->om); cudaFree(r->eb);
+            delete r;
+            return rc;
+        }
+        fresh = true;
+    }
+    auto fail = [&](int code) {
+        if (fresh) { cudaFree(r->om); cudaFree(r->eb); delete r; }
+        return code;
+    };
+    std::memset(&r->counts, 0, sizeof(r->counts));
+    r->phase_rounds.clear();
+
+    Pipeline P;
+    P.ctx = ctx;
+    P.g = g;
+    P.t = &t;
+    build_dev_tmpl(t, P.dt);
+    P.maxc = P.dt.n_cls;
+    cudaStream_t s = ctx->stream;
+
+#define CUF(call)                                                                       \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_err(ctx, CCPM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return fail(CCPM_ECUDA);                                                    \
+        }                                                                               \
+    } while (0)
+#define RCF(expr)                     \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_) return fail(rc_);    \
+    } while (0)
+
+    CUF(cudaEventRecord(w.ev[0], s));
+    // ---- init (Alg. 3)
+    LabelMask lm;
+    std::memset(&lm, 0, sizeof(lm));
+    for (int q = 0; q < t.n0; q++) lm.m[t.labels[q]] |= 1u << q;
+    CUF(cudaMemsetAsync(w.ebits, 0xFF, sizeof(uint32_t) * (size_t)w.words, s));
+    // no entries past m_dir: padding bits of the last word and the guard word stay 0
+    k_set_word<<<1, 1, 0, s>>>(w.ebits + w.words, 0u);
+    P.launches += 1 + ((g->m & 31) != 0);
+    if (g->m & 31) k_set_word<<<1, 1, 0, s>>>(w.ebits + w.words - 1, (1u << (uint32_t)(g->m & 31)) - 1u);
+    CUF(cudaGetLastError());
+    CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+    {
+        int grid = grid_for(ctx, g->n, 256, 8);
+        P.launches++;
+        k_init<<<grid, 256, 0, s>>>(g->n, g->rp, g->lab, lm, w.om[0], w.om[1], w.small[0], w.med[0],
+                                    w.chunk[0], w.st, hub_deg);
+        CUF(cudaGetLastError());
+    }
+    RCF(P.read_stats());
+    P.cur = 0;
+    P.li = 0;
+    P.n_small = w.st_h->n_small;
+    P.n_med = w.st_h->n_med;
+    P.n_chunk = w.st_h->n_chunk;
+    if (w.st_h->n_hub_slots > (unsigned)w.acc_cap || P.n_chunk > w.chunk_cap)
+        return fail(set_err(ctx, CCPM_EOVERFLOW, "hub bookkeeping overflow"));
+
+    // ---- LCC to fixpoint (Alg. 4)
+    int64_t rounds = 0;
+    RCF(P.lcc(&rounds));
+    r->phase_rounds.push_back((int32_t)rounds);
+    int64_t total_rounds = rounds;
+    CUF(cudaEventRecord(w.ev[1], s));
+
+    // ---- non-local constraints, one at a time (Alg. 1, Alg. 6/7)
+    int64_t tokens = 0;
+    bool over = false;
+    int nl_run = 0;
+    std::vector<int> order = t.order;
+    for (size_t ci = 0; ci < order.size(); ci++) {
+        const HostConstraint &c = t.k0[(size_t)order[ci]];
+        uint32_t sadj[kMaxT] = {};
+        for (auto &e : c.edges) { sadj[e.first] |= 1u << e.second; sadj[e.second] |= 1u << e.first; }
+        for (int h = 0; h < kMaxT; h++)
+            if ((c.hmask >> h) & 1u) build_plan(t, c.vmask, sadj, h, g->label_freq, false, w.plans_h[h]);
+        CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * kMaxT, cudaMemcpyHostToDevice, s));
+        CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+        P.launches++;
+        k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], c.hmask, w.roots, w.st);
+        CUF(cudaGetLastError());
+        RCF(P.read_stats());
+        const int64_t n_roots = w.st_h->n_roots;
+        nl_run++;
+        if (n_roots > 0) {
+            SearchArgs a{};
+            a.rp = g->rp;
+            a.col = g->col;
+            a.om = w.om[P.cur];
+            a.ebits = w.ebits;
+            a.roots = w.roots;
+            a.n_roots = n_roots;
+            a.plans = w.plans;
+            a.heads = c.hmask;
+            a.sat = w.sat;
+            a.st = w.st;
+            a.budget = budget;
+            P.launches++;
+            k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            CUF(cudaGetLastError());
+            P.launches++;
+            k_nlcc_apply<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, c.hmask, w.sat,
+                                                                        w.om[0], w.om[1], g->rp, w.ebits, w.st);
+            CUF(cudaGetLastError());
+            RCF(P.read_stats());
+            if (w.st_h->overflow) over = true;
+            P.windows += (int64_t)w.st_h->windows;
+            tokens += (int64_t)w.st_h->tokens;
+        }
+        bool changed = n_roots > 0 && w.st_h->changed;
+        int64_t rr = 0;
+        if (changed) {
+            // the previous fixpoint's frontier holds every live vertex
+            RCF(P.lcc(&rr));
+        }
+        r->phase_rounds.push_back((int32_t)rr);
+        total_rounds += rr;
+    }
+    CUF(cudaEventRecord(w.ev[2], s));
+
+    // ---- final template-driven search and match count (Remark 1, Sec. 4.6)
+    bool count_valid = false;
+    uint64_t matches = 0;
+    bool final_done = false;
+    if (opt.run_final) {
+        int root = 0;
+        for (int q = 1; q < t.n0; q++) {
+            if (g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]]) root = q;
+        }
+        uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
+        build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0]);
+        CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan), cudaMemcpyHostToDevice, s));
+        CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+        CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
+        CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
+        P.launches++;
+        k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], 1u << root, w.roots, w.st);
+        CUF(cudaGetLastError());
+        RCF(P.read_stats());
+        const int64_t n_roots = w.st_h->n_roots;
+        if (n_roots > 0) {
+            SearchArgs a{};
+            a.rp = g->rp;
+            a.col = g->col;
+            a.om = w.om[P.cur];
+            a.ebits = w.ebits;
+            a.roots = w.roots;
+            a.n_roots = n_roots;
+            a.plans = w.plans;
+            a.heads = 1u << root;
+            a.om_out = r->om;
+            a.eb_out = r->eb;
+            a.st = w.st;
+            a.budget = budget;
+            a.cap = opt.max_embeddings;
+            P.launches++;
+            k_final_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            CUF(cudaGetLastError());
+            RCF(P.read_stats());
+        }
+        P.windows += (int64_t)w.st_h->windows;
+        matches = w.st_h->matches;
+        count_valid = !w.st_h->overflow;
+        final_done = count_valid;
+    }
+    if (!final_done) {
+        // hand back the pruned state: exact edge map for live rows, dead rows zeroed
+        P.launches++;
+        k_materialize<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, g->col, w.ebits);
+        CUF(cudaGetLastError());
+        CUF(cudaMemcpyAsync(r->om, w.om[P.cur], sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+        CUF(cudaMemcpyAsync(r->eb, w.ebits, sizeof(uint32_t) * (size_t)w.words, cudaMemcpyDeviceToDevice, s));
+    }
+    CUF(cudaEventRecord(w.ev[3], s));
+    CUF(cudaMemsetAsync(w.cnt, 0, 2 * sizeof(unsigned long long), s));
+    P.launches++;
+    k_count<<<grid_for(ctx, std::max<int64_t>(g->n, w.words), 256, 8), 256, 0, s>>>(g->n, r->om, w.words, r->eb, w.cnt);
+    CUF(cudaGetLastError());
+    CUF(cudaMemcpyAsync(w.cnt_h, w.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CUF(cudaStreamSynchronize(s));
+    float ms_lcc = 0, ms_nlcc = 0, ms_final = 0;
+    cudaEventElapsedTime(&ms_lcc, w.ev[0], w.ev[1]);
+    cudaEventElapsedTime(&ms_nlcc, w.ev[1], w.ev[2]);
+    cudaEventElapsedTime(&ms_final, w.ev[2], w.ev[3]);
+
+    ccpm_counts &cn = r->counts;
+    cn.active_v = (int64_t)w.cnt_h[0];
+    cn.active_e_dir = (int64_t)w.cnt_h[1];
+    cn.lcc_rounds_total = total_rounds;
+    cn.n_phases = (int32_t)r->phase_rounds.size();
+    cn.nlcc_constraints_run = nl_run;
+    cn.count_valid = count_valid ? 1 : 0;
+    cn.match_embeddings = count_valid ? matches : 0;
+    cn.automorphisms = t.automorphisms;
+    cn.match_subgraphs = (count_valid && t.automorphisms) ? matches / t.automorphisms : 0;
+    cn.tokens = tokens;
+    cn.edges_scanned_lcc = P.scanned;
+    cn.edges_scanned_search = P.windows;
+    cn.ms_lcc = ms_lcc;
+    cn.ms_nlcc = ms_nlcc;
+    cn.ms_final = ms_final;
+    cn.ms_total = (double)ms_lcc + ms_nlcc + ms_final;
+    cn.lcc_launches = P.lcc_launches;
+    cn.ms_lcc_kernel = P.ms_lcc_kernel;
+    cn.lcc_row_entries = P.rows;
+    cn.lcc_active_vertices = P.alive;
+    cn.lcc_alg_bytes = 24 * P.alive + 4 * P.rows + P.rows / 8 + 4 * P.scanned;
+    cn.kernel_launches = P.launches;
+    int status = CCPM_OK;
+    if (over || (opt.run_final && !count_valid)) status = CCPM_EBUDGET;
+    cn.status = status;
+    *out = r;
+    if (status == CCPM_EBUDGET) set_err(ctx, CCPM_EBUDGET, "a search budget was exceeded");
+    return status;
+#undef CUF
+#undef RCF
+}
+
+int ccpm_result_omega(ccpm_result_t r, uint32_t *dst, int64_t n, int dst_on_device) {
+    if (!r || !dst || n != r->g->n) return CCPM_EINVAL;
+    ccpm_ctx *ctx = r->g->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaMemcpyAsync(dst, r->om, sizeof(uint32_t) * (size_t)n,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return CCPM_OK;
+}
+
+int ccpm_result_edge_bitmap(ccpm_result_t r, uint32_t *dst, int64_t words, int dst_on_device) {
+    if (!r || !dst || words != r->g->ws.words) return CCPM_EINVAL;
+    ccpm_ctx *ctx = r->g->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaMemcpyAsync(dst, r->eb, sizeof(uint32_t) * (size_t)words,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return CCPM_OK;
+}
+
+int ccpm_result_counts(ccpm_result_t r, ccpm_counts *out) {
+    if (!r || !out) return CCPM_EINVAL;
+    *out = r->counts;
+    return CCPM_OK;
+}
+
+int ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap) {
+    if (!r || (!dst && cap > 0)) return CCPM_EINVAL;
+    int k = std::min(cap, (int)r->phase_rounds.size());
+    for (int i = 0; i < k; i++) dst[i] = r->phase_rounds[(size_t)i];
+    return CCPM_OK;
+}
+
+const uint32_t *ccpm_result_omega_device(ccpm_result_t r) { return r ? r->om : nullptr; }
+const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r) { return r ? r->eb : nullptr; }
+
+void ccpm_result_destroy(ccpm_result_t r) {
+    if (!r) return;
+    cudaSetDevice(r->g->ctx->device);
+    cudaFree(r->om);
+    cudaFree(r->eb);
+    delete r;
+}
+
+}  // extern "C"
