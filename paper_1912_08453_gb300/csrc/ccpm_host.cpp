@@ -364,6 +364,7 @@ void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int roo
     for (int i = 0; i < kMaxT; i++) pos_of[i] = -1;
     int k = 0;
     p.q[k] = (int8_t)root;
+    p.lab[k] = t.labels[root];
     p.par[k] = -1;
     pos_of[root] = k++;
     uint32_t placed = 1u << root;
@@ -390,6 +391,8 @@ void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int roo
             if (t.labels[qj] == t.labels[best]) same |= 1u << j;
         }
         p.q[k] = (int8_t)best;
+        p.lab[k] = t.labels[best];
+        p.nbr[k] = back | (1u << parent_pos);
         p.par[k] = (int8_t)parent_pos;
         p.back[k] = back;
         p.same[k] = same;

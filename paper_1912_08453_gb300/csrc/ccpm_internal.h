@@ -13,7 +13,7 @@ namespace ccpm {
 constexpr int kMaxT = 32;           // template vertices (omega is one uint32)
 constexpr int kMaxCls = 32;         // label-multiplicity classes per template
 constexpr int kSmallDeg = 32;       // rows up to this length: 4 lanes per vertex
-constexpr int kDefaultHubDeg = 4096;// longer rows are split into chunks of this size
+constexpr int kDefaultHubDeg = 1024;// longer rows are split into chunks of this size
 constexpr uint64_t kDefaultSearchBudget = 1ull << 22;
 
 // Template tables for the LCC kernels.  A "class" is (q, L) with
@@ -37,6 +37,8 @@ struct DevPlan {
     int k;
     int8_t q[kMaxT];
     int8_t par[kMaxT];
+    uint8_t lab[kMaxT];       // label of the template vertex at each position
+    uint32_t nbr[kMaxT];      // earlier positions joined to position i in S
     uint32_t back[kMaxT];
     uint32_t same[kMaxT];
     // full-template enumeration marks these (position, position) edges

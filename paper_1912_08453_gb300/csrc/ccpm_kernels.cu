@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <cub/device/device_segmented_sort.cuh>
+
 #include "ccpm_internal.h"
 
 namespace ccpm {
@@ -227,7 +229,7 @@ __device__ __forceinline__ void scan_entries(int64_t beg, int64_t end, uint32_t 
                                              const uint32_t *__restrict__ om, uint32_t *ebits,
                                              const SmemTmpl &s, Partial<MAXC> &p,
                                              unsigned long long &scanned) {
-    constexpr int UNR = 4;
+    constexpr int UNR = G >= 32 ? 8 : 4;   // entries in flight per lane
     for (int64_t base = beg + lane_g; base < end; base += (int64_t)G * UNR) {
         uint32_t word[UNR];
         int32_t u[UNR];
@@ -432,18 +434,29 @@ k_lcc_round(LccArgs a, DevTmpl t) {
 
 // -------------------------------------------------------------------------
 // Rooted injective embedding search (NLCC token walk, Alg. 6/7, and the
-// final template-driven search, Remark 1).  One warp per root vertex; the
-// warp walks the plan depth first, testing 32 neighbours of the anchor at a
-// time in parallel.
+// final template-driven search, Remark 1).  One warp per root vertex, roots
+// handed out dynamically; the warp walks the plan depth first, testing 32
+// candidates at a time in parallel.
+//
+// Searches run only at LCC fixpoints.  There an entry (x, u) is active
+// exactly when some template edge joins omega(x) and omega(u) (edge
+// elimination has removed every other entry and keeps every such one), so a
+// search needs adjacency and omega only: a candidate u for template vertex q
+// next to a placed x with q_x in omega(x) is joined to x by an active entry
+// iff u is a neighbour of x with q in omega(u).  Candidates are read from a
+// copy of every row grouped by neighbour label (label, then id), so only the
+// neighbours that carry label(q) are ever scanned.
 // -------------------------------------------------------------------------
 
 struct SearchArgs {
     const int64_t *rp;
-    const int32_t *col;
+    const int32_t *col;       // id-sorted rows (edge-bitmap indexing)
+    const int32_t *lcol;      // rows grouped by neighbour label, ids ascending inside a group
+    const uint8_t *nlab;      // label of lcol[e]
     const uint32_t *om;
-    const uint32_t *ebits;
     const int32_t *roots;
     int64_t n_roots;
+    unsigned long long *next_root;   // dynamic work counter
     const DevPlan *plans;     // plans[h] for each head h (NLCC) or plans[0] (final)
     uint32_t heads;           // NLCC: heads of the constraint; final: 1 << plans[0].q[0]
     uint32_t *sat;            // NLCC output: satisfied heads per vertex
@@ -456,17 +469,44 @@ struct SearchArgs {
 
 struct WarpSearch {
     int32_t psi[kMaxT];
-    int32_t cand[kMaxT][32];
-    int64_t pos[kMaxT];
+    int64_t pos[kMaxT];       // next window start inside the chosen label range
     int64_t end[kMaxT];
-    uint32_t mask[kMaxT];
+    int64_t wbase[kMaxT];     // start of the window the mask refers to
+    uint32_t mask[kMaxT];     // untried valid candidates of that window
+    uint32_t chk[kMaxT];      // placed neighbours still to be tested by lookup
 };
 
-__device__ __forceinline__ bool ebit(const uint32_t *eb, int64_t e) {
-    return (eb[e >> 5] >> (uint32_t)(e & 31)) & 1u;
+// [lo, hi) of the label-L group in the label-grouped row of x.
+__device__ __forceinline__ void label_range(const int64_t *rp, const uint8_t *nlab, int32_t x, uint32_t L,
+                                            int64_t &lo, int64_t &hi) {
+    const int64_t a = rp[x], b = rp[x + 1];
+    int64_t l = a, h = b;
+    while (l < h) {
+        int64_t m = (l + h) >> 1;
+        if ((uint32_t)__ldg(nlab + m) < L) l = m + 1; else h = m;
+    }
+    lo = l;
+    h = b;
+    while (l < h) {
+        int64_t m = (l + h) >> 1;
+        if ((uint32_t)__ldg(nlab + m) <= L) l = m + 1; else h = m;
+    }
+    hi = l;
 }
 
-// CSR entry index of (x, y) or -1: binary search over the sorted row of x.
+// Is u (label L) a neighbour of x?  Binary search inside x's label-L group.
+__device__ __forceinline__ bool adjacent(const SearchArgs &a, int32_t x, int32_t u, uint32_t L) {
+    int64_t lo, hi;
+    label_range(a.rp, a.nlab, x, L, lo, hi);
+    const int64_t stop = hi;
+    while (lo < hi) {
+        int64_t m = (lo + hi) >> 1;
+        if (__ldg(a.lcol + m) < u) lo = m + 1; else hi = m;
+    }
+    return lo < stop && __ldg(a.lcol + lo) == u;
+}
+
+// CSR entry index of (x, y) in the id-sorted rows, or -1.
 __device__ __forceinline__ int64_t find_entry(const int64_t *rp, const int32_t *col, int32_t x, int32_t y) {
     int64_t lo = rp[x], hi = rp[x + 1];
     const int64_t stop = hi;
@@ -477,69 +517,86 @@ __device__ __forceinline__ int64_t find_entry(const int64_t *rp, const int32_t *
     return (lo < stop && __ldg(col + lo) == y) ? lo : -1;
 }
 
-// Active edge between x and y?  Searches the shorter of the two rows.
-__device__ __forceinline__ bool edge_active(const int64_t *rp, const int32_t *col, const uint32_t *eb,
-                                            int32_t x, int32_t y) {
-    int64_t dx = rp[x + 1] - rp[x], dy = rp[y + 1] - rp[y];
-    int64_t e = dx <= dy ? find_entry(rp, col, x, y) : find_entry(rp, col, y, x);
-    return e >= 0 && ebit(eb, e);
+// Open level d: among the placed neighbours of position d pick the one whose
+// label group is shortest; scan that group, look the others up.
+__device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P, WarpSearch &W, int d) {
+    const int lane = (int)lane_id();
+    const uint32_t cm = P.nbr[d];
+    const int cnt = __popc(cm);
+    int64_t lo = 0, hi = 0, len = INT64_MAX;
+    int j = -1;
+    if (lane < cnt) {
+        uint32_t m = cm;
+        for (int i = 0; i < lane; i++) m &= m - 1u;
+        j = __ffs(m) - 1;
+        label_range(a.rp, a.nlab, W.psi[j], P.lab[d], lo, hi);
+        len = hi - lo;
+    }
+    int best = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+        int64_t ol = __shfl_xor_sync(FULL_MASK, len, o);
+        int ob = __shfl_xor_sync(FULL_MASK, best, o);
+        if (ol < len || (ol == len && ob < best)) { len = ol; best = ob; }
+    }
+    lo = __shfl_sync(FULL_MASK, lo, best);
+    hi = __shfl_sync(FULL_MASK, hi, best);
+    j = __shfl_sync(FULL_MASK, j, best);
+    if (lane == 0) {
+        W.pos[d] = lo;
+        W.end[d] = hi;
+        W.mask[d] = 0u;
+        W.chk[d] = cm & ~(1u << j);
+    }
+    __syncwarp();
 }
 
 // Returns true if an embedding exists (ENUM = false) / after enumerating all
-// embeddings from this root (ENUM = true).  *over is set when the window
+// embeddings from this root (ENUM = true).  `over` is set when the window
 // budget ran out; for existence the root is then reported as satisfied, which
 // keeps the result a superset of the exact answer.
 template <bool ENUM>
 __device__ bool search_root(const SearchArgs &a, const DevPlan &P, int32_t root, WarpSearch &W,
-                            unsigned long long &windows, unsigned long long &matches, bool &over) {
+                            unsigned long long &entries, unsigned long long &matches, bool &over) {
     const int lane = (int)lane_id();
     const int k = P.k;
     uint64_t used = 0;
-    if (lane == 0) {
-        W.psi[0] = root;
-        int32_t anchor = root;
-        W.pos[1] = a.rp[anchor];
-        W.end[1] = a.rp[anchor + 1];
-        W.mask[1] = 0u;
-    }
+    if (lane == 0) W.psi[0] = root;
     __syncwarp();
+    open_level(a, P, W, 1);
     int d = 1;
     while (d >= 1) {
-        uint32_t m = W.mask[d];
+        const uint32_t m = W.mask[d];
         if (m == 0u) {
             const int64_t pos = W.pos[d], end = W.end[d];
             if (pos >= end) { d--; continue; }
             if (++used > a.budget) { over = true; return !ENUM; }
-            windows += (unsigned long long)min((int64_t)32, end - pos);
+            entries += (unsigned long long)min((int64_t)32, end - pos);
             const int64_t e = pos + lane;
             const int q = P.q[d];
             bool ok = false;
-            int32_t u = -1;
-            if (e < end && ebit(a.ebits, e)) {
-                u = __ldg(a.col + e);
+            if (e < end) {
+                const int32_t u = __ldg(a.lcol + e);
                 if ((__ldg(a.om + u) >> q) & 1u) {
                     ok = true;
                     for (uint32_t sm = P.same[d]; sm && ok; sm &= sm - 1u)
                         if (W.psi[__ffs(sm) - 1] == u) ok = false;
-                    for (uint32_t bm = P.back[d]; bm && ok; bm &= bm - 1u)
-                        ok = edge_active(a.rp, a.col, a.ebits, W.psi[__ffs(bm) - 1], u);
+                    for (uint32_t bm = W.chk[d]; bm && ok; bm &= bm - 1u)
+                        ok = adjacent(a, W.psi[__ffs(bm) - 1], u, P.lab[d]);
                 }
             }
             const uint32_t vm = __ballot_sync(FULL_MASK, ok);
-            W.cand[d][lane] = u;
-            __syncwarp();
-            if (lane == 0) { W.mask[d] = vm; W.pos[d] = pos + 32; }
+            if (lane == 0) { W.mask[d] = vm; W.wbase[d] = pos; W.pos[d] = pos + 32; }
             __syncwarp();
             continue;
         }
         const int b = __ffs(m) - 1;
-        if (lane == 0) { W.mask[d] = m & (m - 1u); W.psi[d] = W.cand[d][b]; }
+        if (lane == 0) { W.mask[d] = m & (m - 1u); W.psi[d] = __ldg(a.lcol + W.wbase[d] + b); }
         __syncwarp();
         if (d == k - 1) {
             if (!ENUM) return true;
             matches++;
             // mark the match: omega*(psi(i)) gets q_i, both directions of
-            // every template edge get their bit
+            // every template edge get their bit (id-sorted entry indices)
             if (lane < k) {
                 int32_t x = W.psi[lane];
                 uint32_t bit = 1u << P.q[lane];
@@ -562,15 +619,15 @@ __device__ bool search_root(const SearchArgs &a, const DevPlan &P, int32_t root,
             continue;
         }
         d++;
-        if (lane == 0) {
-            int32_t anchor = W.psi[P.par[d]];
-            W.pos[d] = a.rp[anchor];
-            W.end[d] = a.rp[anchor + 1];
-            W.mask[d] = 0u;
-        }
-        __syncwarp();
+        open_level(a, P, W, d);
     }
     return false;
+}
+
+__device__ __forceinline__ int64_t grab_root(const SearchArgs &a) {
+    unsigned long long r = 0;
+    if (lane_id() == 0) r = atomicAdd(a.next_root, 1ull);
+    return (int64_t)__shfl_sync(FULL_MASK, r, 0);
 }
 
 __global__ void __launch_bounds__(128)
@@ -579,28 +636,25 @@ k_nlcc_search(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long windows = 0, matches = 0, tokens = 0;
+    unsigned long long entries = 0, matches = 0, tokens = 0;
     bool over = false;
-    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+    for (int64_t it = grab_root(a); it < a.n_roots; it = grab_root(a)) {
         const int32_t v = a.roots[it];
         const uint32_t hv = __ldg(a.om + v) & a.heads;
         tokens += (unsigned long long)__popc(hv);
         uint32_t sat = 0;
         for (uint32_t hm = hv; hm; hm &= hm - 1u) {
             const int h = __ffs(hm) - 1;
-            if (search_root<false>(a, a.plans[h], v, W, windows, matches, over)) sat |= 1u << h;
+            if (search_root<false>(a, a.plans[h], v, W, entries, matches, over)) sat |= 1u << h;
             __syncwarp();
         }
         if (lane == 0) a.sat[v] = sat;
     }
-    for (int o = 16; o > 0; o >>= 1) windows += __shfl_xor_sync(FULL_MASK, windows, o);
-    uint32_t ov = __ballot_sync(FULL_MASK, over);
+    // entries, tokens and over are identical in every lane of the warp
     if (lane == 0) {
-        if (windows) atomicAdd(&a.st->windows, windows);
+        if (entries) atomicAdd(&a.st->windows, entries);
         if (tokens) atomicAdd(&a.st->tokens, tokens);
-        if (ov) atomicOr(&a.st->overflow, 1u);
+        if (over) atomicOr(&a.st->overflow, 1u);
     }
 }
 
@@ -610,17 +664,15 @@ k_final_search(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long windows = 0, matches = 0;
+    unsigned long long entries = 0, matches = 0;
     bool over = false;
-    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+    for (int64_t it = grab_root(a); it < a.n_roots; it = grab_root(a)) {
         unsigned int stop = 0;
         if (lane == 0) stop = *(volatile unsigned int *)&a.st->overflow;
         if (__shfl_sync(FULL_MASK, stop, 0)) break;
         const int32_t v = a.roots[it];
         unsigned long long before = matches;
-        search_root<true>(a, a.plans[0], v, W, windows, matches, over);
+        search_root<true>(a, a.plans[0], v, W, entries, matches, over);
         __syncwarp();
         if (matches != before) {
             unsigned long long tot = 0;
@@ -633,8 +685,15 @@ k_final_search(SearchArgs a) {
             break;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) windows += __shfl_xor_sync(FULL_MASK, windows, o);
-    if (lane == 0 && windows) atomicAdd(&a.st->windows, windows);
+    if (lane == 0 && entries) atomicAdd(&a.st->windows, entries);
+}
+
+// Label of the neighbour at every CSR entry (sort keys for the grouped rows).
+__global__ void __launch_bounds__(256)
+k_gather_labels(int64_t m, const int32_t *__restrict__ col, const uint8_t *__restrict__ lab, uint8_t *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+        out[e] = __ldg(lab + __ldg(col + e));
 }
 
 // Roots of a search: every vertex whose omega meets `heads`.
@@ -676,6 +735,10 @@ k_nlcc_apply(const int32_t *__restrict__ roots, int64_t n_roots, uint32_t heads,
         }
     }
     if (__any_sync(FULL_MASK, changed) && lane_id() == 0) atomicOr(&st->changed, 1u);
+}
+
+__device__ __forceinline__ bool ebit(const uint32_t *eb, int64_t e) {
+    return (eb[e >> 5] >> (uint32_t)(e & 31)) & 1u;
 }
 
 // Make the edge map exact everywhere (used when it is handed back without the
@@ -752,6 +815,7 @@ struct Workspace {
     uint32_t *sat = nullptr;
     DevPlan *plans = nullptr;
     RoundStats *st = nullptr;        // device
+    unsigned long long *next_root = nullptr;   // dynamic root counter of the searches
     RoundStats *st_h = nullptr;      // pinned host mirror
     unsigned long long *cnt = nullptr;
     unsigned long long *cnt_h = nullptr;
@@ -767,6 +831,8 @@ struct ccpm_graph {
     uint8_t *lab = nullptr;
     bool borrowed = false;
     int64_t label_freq[256] = {};
+    int32_t *lcol = nullptr;      // rows grouped by neighbour label (built on first search)
+    uint8_t *nlab = nullptr;
     Workspace ws;
 };
 
@@ -814,7 +880,7 @@ void ws_free(Workspace &w) {
     cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.ebits);
     cudaFree(w.small[0]); cudaFree(w.small[1]); cudaFree(w.med[0]); cudaFree(w.med[1]);
     cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
-    cudaFree(w.sat); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt);
+    cudaFree(w.sat); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
     if (w.st_h) cudaFreeHost(w.st_h);
     if (w.cnt_h) cudaFreeHost(w.cnt_h);
     if (w.plans_h) cudaFreeHost(w.plans_h);
@@ -847,11 +913,44 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxT))) return rc;
     if ((rc = dalloc(ctx, &w.st, 1))) return rc;
     if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
+    if ((rc = dalloc(ctx, &w.next_root, 1))) return rc;
     CU(ctx, cudaMallocHost((void **)&w.st_h, sizeof(RoundStats)));
     CU(ctx, cudaMallocHost((void **)&w.cnt_h, 2 * sizeof(unsigned long long)));
     CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxT * sizeof(DevPlan)));
     CU(ctx, cudaMemsetAsync(w.acc, 0, sizeof(HubAcc) * (size_t)w.acc_cap, ctx->stream));
     for (auto &e : w.ev) CU(ctx, cudaEventCreate(&e));
+    return CCPM_OK;
+}
+
+// Label-grouped copy of the rows: a stable segmented sort of every row by the
+// neighbours' labels keeps ids ascending inside each label group.  Built once
+// per graph, the first time a search needs it.
+int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
+    if (g->lcol || g->m == 0) return CCPM_OK;
+    int rc;
+    uint8_t *keys = nullptr;
+    if ((rc = dalloc(ctx, &g->lcol, (size_t)g->m))) return rc;
+    if ((rc = dalloc(ctx, &g->nlab, (size_t)g->m))) return rc;
+    if ((rc = dalloc(ctx, &keys, (size_t)g->m))) return rc;
+    int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_gather_labels<<<grid, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, keys);
+    size_t tmp_bytes = 0;
+    cudaError_t e = cub::DeviceSegmentedSort::StableSortPairs(nullptr, tmp_bytes, keys, g->nlab, g->col, g->lcol,
+                                                              g->m, g->n, g->rp, g->rp + 1, ctx->stream);
+    void *tmp = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 1);
+    if (e == cudaSuccess)
+        e = cub::DeviceSegmentedSort::StableSortPairs(tmp, tmp_bytes, keys, g->nlab, g->col, g->lcol,
+                                                      g->m, g->n, g->rp, g->rp + 1, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    cudaFree(keys);
+    if (e != cudaSuccess) {
+        cudaFree(g->lcol); cudaFree(g->nlab);
+        g->lcol = nullptr; g->nlab = nullptr;
+        return set_err(ctx, e == cudaErrorMemoryAllocation ? CCPM_ENOMEM : CCPM_ECUDA,
+                       std::string("label-grouped rows: ") + cudaGetErrorString(e));
+    }
     return CCPM_OK;
 }
 
@@ -1068,6 +1167,8 @@ void ccpm_graph_destroy(ccpm_graph_t g) {
     cudaSetDevice(g->ctx->device);
     ws_free(g->ws);
     if (!g->borrowed) { cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab); }
+    cudaFree(g->lcol);
+    cudaFree(g->nlab);
     delete g;
 }
 
@@ -1248,13 +1349,17 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         const int64_t n_roots = w.st_h->n_roots;
         nl_run++;
         if (n_roots > 0) {
+            RCF(ensure_label_rows(ctx, g));
+            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             SearchArgs a{};
             a.rp = g->rp;
             a.col = g->col;
+            a.lcol = g->lcol;
+            a.nlab = g->nlab;
             a.om = w.om[P.cur];
-            a.ebits = w.ebits;
             a.roots = w.roots;
             a.n_roots = n_roots;
+            a.next_root = w.next_root;
             a.plans = w.plans;
             a.heads = c.hmask;
             a.sat = w.sat;
@@ -1304,13 +1409,17 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         RCF(P.read_stats());
         const int64_t n_roots = w.st_h->n_roots;
         if (n_roots > 0) {
+            RCF(ensure_label_rows(ctx, g));
+            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             SearchArgs a{};
             a.rp = g->rp;
             a.col = g->col;
+            a.lcol = g->lcol;
+            a.nlab = g->nlab;
             a.om = w.om[P.cur];
-            a.ebits = w.ebits;
             a.roots = w.roots;
             a.n_roots = n_roots;
+            a.next_root = w.next_root;
             a.plans = w.plans;
             a.heads = 1u << root;
             a.om_out = r->om;
