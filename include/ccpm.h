@@ -192,6 +192,38 @@ const uint32_t *ccpm_result_omega_device(ccpm_result_t r);
 const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r);
 void ccpm_result_destroy(ccpm_result_t r);
 
+/* ------------------------------------------------- allocation-free LCC */
+
+/* Local constraint checking to its fixpoint without allocating anything.
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory while they run (a memory budget fixed up front,
+ * an allocator owned by someone else, or host code that may not block inside
+ * cudaMalloc).
+ *
+ * Inputs are device pointers on `device`: the CSR graph (row_ptr int64 [n+1],
+ * col int32 [m_dir], labels uint8 [n], same rules as ccpm_graph_load_csr) and
+ * the template as host arrays (n0 labels, m0 edges as 2*m0 int32).  Outputs:
+ * omega (device, n uint32) and ebits (device, ceil(m_dir/32) uint32 words),
+ * both in the layouts described at the top of this file; *rounds (host,
+ * nullable) gets the LCC rounds executed including the final quiescent one,
+ * *edges_scanned (host, nullable) the active entries read over all rounds.
+ * The result equals the LCC fixpoint ccpm_prune reaches before any
+ * non-local constraint.  Work runs on `cuda_stream` (NULL: the legacy default
+ * stream) and the call returns when it is done.
+ *
+ * Scratch lives in a fixed 16 MiB area compiled into the library, enough for
+ * roughly n <= 500,000 vertices and m_dir <= 16,000,000 entries; larger graphs
+ * are rejected with CCPM_EINVAL and a message in errbuf (nullable, errlen
+ * bytes, written by every call).  The first call on a device looks up the
+ * area's device address (make that first call before any stream capture).
+ * All calls share the one area: calls whose GPU work overlaps in time, on any
+ * streams, corrupt each other's results, so serialise them. */
+int  ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t n, int64_t m_dir,
+                               const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
+                               int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,
+                               uint32_t *omega, uint32_t *ebits, int32_t *rounds,
+                               int64_t *edges_scanned, char *errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

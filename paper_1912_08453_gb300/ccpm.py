@@ -86,6 +86,8 @@ def _load():
         "ccpm_result_omega_device": ([vp], vp),
         "ccpm_result_edge_bitmap_device": ([vp], vp),
         "ccpm_result_destroy": ([vp], None),
+        "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
+                                       P(ctypes.c_int32), P(ctypes.c_int64), ctypes.c_char_p, ctypes.c_size_t], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -102,7 +104,7 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_constraints_generate", "ccpm_constraints_describe", "ccpm_tmpl_set_order",
             "ccpm_prune", "ccpm_result_omega", "ccpm_result_edge_bitmap", "ccpm_result_counts",
             "ccpm_result_phase_rounds", "ccpm_result_omega_device",
-            "ccpm_result_edge_bitmap_device", "ccpm_result_destroy"]
+            "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc"]
 
 
 def _ptr(a):
@@ -293,3 +295,26 @@ def prune(ctx: Context, graph: Graph, tmpl: Template, opts: Options | None = Non
     if result is not None:
         return result
     return Result(graph, h)
+
+
+def lcc_fixpoint_noalloc(device, row_ptr, col, labels, tmpl_labels, tmpl_edges, omega, ebits, stream=None):
+    """ccpm_lcc_fixpoint_noalloc: LCC to its fixpoint with no allocation inside
+    the library, for callers that cannot allocate device memory while they
+    run.  Graph arrays and the omega / ebits outputs are CUDA tensors the
+    caller owns.  Returns (rounds, edges_scanned)."""
+    tl = np.ascontiguousarray(np.asarray(tmpl_labels, dtype=np.uint8))
+    te = np.ascontiguousarray(np.asarray(tmpl_edges, dtype=np.int32).reshape(-1))
+    ptrs = [_ptr(x) for x in (row_ptr, col, labels, omega, ebits)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("graph arrays and outputs must be device tensors")
+    rounds = ctypes.c_int32()
+    scanned = ctypes.c_int64()
+    err = ctypes.create_string_buffer(256)
+    rc = lib.ccpm_lcc_fixpoint_noalloc(int(device), ctypes.c_void_p(int(stream)) if stream else None,
+                                       int(row_ptr.shape[0]) - 1, int(col.shape[0]),
+                                       ptrs[0][0], ptrs[1][0], ptrs[2][0], int(tl.shape[0]), _ptr(tl)[0],
+                                       int(te.shape[0] // 2), _ptr(te)[0], ptrs[3][0], ptrs[4][0],
+                                       ctypes.byref(rounds), ctypes.byref(scanned), err, 256)
+    if rc:
+        raise CcpmError(rc, f"ccpm_lcc_fixpoint_noalloc: {err.value.decode()}")
+    return rounds.value, scanned.value

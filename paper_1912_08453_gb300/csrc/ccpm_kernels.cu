@@ -1535,3 +1535,230 @@ void ccpm_result_destroy(ccpm_result_t r) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free LCC entry point
+//
+// Some callers cannot allocate device memory while they run: code that works
+// inside a memory budget reserved up front, host code holding a lock in which
+// cudaMalloc may block on the driver, or applications whose allocator is
+// owned by someone else.  ccpm_lcc_fixpoint_noalloc runs local constraint
+// checking to its fixpoint using only the caller's inputs and outputs plus a
+// fixed scratch area compiled into this library.
+// ===========================================================================
+
+#include <mutex>
+
+namespace {
+
+// Scratch of the allocation-free entry point: the second omega buffer, the
+// frontier lists, the split-row accumulators and the round counters.  It is
+// part of the library image, so every GPU on which the library's kernels are
+// loaded holds these bytes until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct NoAllocLayout {
+    size_t om2, small[2], med[2], chunk[2], acc, st, total;
+    int64_t chunk_cap, acc_cap;
+};
+
+NoAllocLayout noalloc_layout(int64_t n, int64_t m, int hub) {
+    NoAllocLayout L{};
+    L.chunk_cap = 2 * (m / hub) + 16;
+    L.acc_cap = m / hub + 16;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = up256(off + bytes); return at; };
+    L.om2 = take(sizeof(uint32_t) * (size_t)n);
+    for (int i = 0; i < 2; i++) L.small[i] = take(sizeof(int32_t) * (size_t)n);
+    for (int i = 0; i < 2; i++) L.med[i] = take(sizeof(int32_t) * (size_t)n);
+    for (int i = 0; i < 2; i++) L.chunk[i] = take(sizeof(ChunkItem) * (size_t)L.chunk_cap);
+    L.acc = take(sizeof(HubAcc) * (size_t)L.acc_cap);
+    L.st = take(sizeof(RoundStats));
+    L.total = off;
+    return L;
+}
+
+// Template tables straight from the caller's arrays (no heap use).
+const char *noalloc_template(int n0, const uint8_t *labels, int m0, const int32_t *edges,
+                             DevTmpl &d, LabelMask &lm) {
+    if (n0 < 2 || n0 > kMaxT) return "template must have 2..32 vertices";
+    if (m0 < 1 || m0 > CCPM_MAX_TMPL_EDGES || !labels || !edges) return "template needs 1..496 edges";
+    std::memset(&d, 0, sizeof(d));
+    std::memset(&lm, 0, sizeof(lm));
+    d.n0 = n0;
+    for (int i = 0; i < m0; i++) {
+        int a = edges[2 * i], b = edges[2 * i + 1];
+        if (a < 0 || b < 0 || a >= n0 || b >= n0 || a == b) return "bad template edge";
+        if ((d.adj[a] >> b) & 1u) return "duplicate template edge";
+        d.adj[a] |= 1u << b;
+        d.adj[b] |= 1u << a;
+    }
+    uint32_t seen = 1u, fr = 1u;
+    while (fr) {
+        uint32_t nx = 0;
+        for (int q = 0; q < n0; q++) if ((fr >> q) & 1u) nx |= d.adj[q];
+        nx &= ~seen;
+        seen |= nx;
+        fr = nx;
+    }
+    if (seen != (n0 == 32 ? 0xFFFFFFFFu : ((1u << n0) - 1u))) return "template is not connected";
+    for (int q = 0; q < n0; q++) {
+        lm.m[labels[q]] |= 1u << q;
+        uint32_t done = 0;
+        for (int b = 0; b < n0; b++) {
+            if (!((d.adj[q] >> b) & 1u) || ((done >> b) & 1u)) continue;
+            uint32_t grp = 0;
+            for (int c = 0; c < n0; c++)
+                if (((d.adj[q] >> c) & 1u) && labels[c] == labels[b]) grp |= 1u << c;
+            done |= grp;
+            if (__builtin_popcount(grp) >= 2) {
+                if (d.n_cls >= kMaxCls) return "template has more than 32 label-multiplicity classes";
+                d.cls_mask[d.n_cls] = grp;
+                d.cls_need[d.n_cls] = (uint32_t)__builtin_popcount(grp);
+                d.cls_q[d.n_cls] = (uint32_t)q;
+                d.n_cls++;
+            }
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t n, int64_t m_dir,
+                                         const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
+                                         int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,
+                                         uint32_t *omega, uint32_t *ebits, int32_t *rounds,
+                                         int64_t *edges_scanned, char *errbuf, size_t errlen) {
+    auto fail = [&](int code, const char *msg) {
+        if (errbuf && errlen) std::snprintf(errbuf, errlen, "%s", msg);
+        return code;
+    };
+    if (errbuf && errlen) errbuf[0] = '\0';
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(CCPM_EINVAL, "device index out of range");
+    if (n < 1 || n >= ((int64_t)1 << 31) || m_dir < 0 || !row_ptr || !labels || !omega ||
+        (m_dir > 0 && (!col || !ebits)))
+        return fail(CCPM_EINVAL, "need 1 <= n < 2^31, m_dir >= 0 and non-NULL device arrays");
+    DevTmpl dt;
+    LabelMask lm;
+    if (const char *why = noalloc_template(n0, tmpl_labels, m0, tmpl_edges, dt, lm)) return fail(CCPM_EINVAL, why);
+    const int hub = kDefaultHubDeg;
+    const NoAllocLayout L = noalloc_layout(n, m_dir, hub);
+    if (L.total > kNoAllocScratchBytes) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg),
+                      "graph too large for the allocation-free entry point: needs %zu bytes of scratch, "
+                      "the fixed area holds %zu", L.total, kNoAllocScratchBytes);
+        return fail(CCPM_EINVAL, msg);
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(CCPM_ECUDA, cudaGetErrorString(e));
+    unsigned char *base = nullptr;
+    {
+        // once per device, with that device current: the device address of the
+        // scratch array (the host-side symbol is only a stand-in)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[device]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return fail(CCPM_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+            g_noalloc_addr[device] = p;
+        }
+        base = (unsigned char *)g_noalloc_addr[device];
+    }
+    int num_sms = 0;
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return fail(CCPM_ECUDA, cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t *om[2] = {omega, (uint32_t *)(base + L.om2)};
+    int32_t *small[2] = {(int32_t *)(base + L.small[0]), (int32_t *)(base + L.small[1])};
+    int32_t *med[2] = {(int32_t *)(base + L.med[0]), (int32_t *)(base + L.med[1])};
+    ChunkItem *chunk[2] = {(ChunkItem *)(base + L.chunk[0]), (ChunkItem *)(base + L.chunk[1])};
+    HubAcc *acc = (HubAcc *)(base + L.acc);
+    RoundStats *st = (RoundStats *)(base + L.st);
+    RoundStats hs;
+    auto grid = [&](int64_t items, int per_block) {
+        int64_t need = (items + per_block - 1) / per_block;
+        return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * 8));
+    };
+    auto read_stats = [&]() {
+        cudaError_t r = cudaMemcpyAsync(&hs, st, sizeof(RoundStats), cudaMemcpyDeviceToHost, s);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+        return r;
+    };
+#define NA_CU(call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return fail(CCPM_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+    const int64_t words = (m_dir + 31) / 32;
+    // the scratch keeps whatever the previous call left: clear what must start at zero
+    NA_CU(cudaMemsetAsync(acc, 0, sizeof(HubAcc) * (size_t)L.acc_cap, s));
+    NA_CU(cudaMemsetAsync(st, 0, sizeof(RoundStats), s));
+    if (words > 0) {
+        NA_CU(cudaMemsetAsync(ebits, 0xFF, sizeof(uint32_t) * (size_t)words, s));
+        if (m_dir & 31) k_set_word<<<1, 1, 0, s>>>(ebits + words - 1, (1u << (uint32_t)(m_dir & 31)) - 1u);
+    }
+    k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, om[0], om[1], small[0], med[0], chunk[0], st, hub);
+    NA_CU(cudaGetLastError());
+    NA_CU(read_stats());
+    if (hs.n_hub_slots > (unsigned)L.acc_cap || (int64_t)hs.n_chunk > L.chunk_cap)
+        return fail(CCPM_EOVERFLOW, "split-row bookkeeping overflow");
+    int64_t n_small = hs.n_small, n_med = hs.n_med, n_chunk = hs.n_chunk, scanned = 0;
+    int cur = 0, li = 0;
+    int32_t r = 0;
+    for (;;) {
+        NA_CU(cudaMemsetAsync(st, 0, sizeof(RoundStats), s));
+        LccArgs a;
+        a.rp = row_ptr;
+        a.col = col;
+        a.om_cur = om[cur];
+        a.om_next = om[cur ^ 1];
+        a.ebits = ebits;
+        a.small_in = small[li];
+        a.med_in = med[li];
+        a.chunk_in = chunk[li];
+        a.n_small = n_small;
+        a.n_med = n_med;
+        a.n_chunk = n_chunk;
+        a.small_out = small[li ^ 1];
+        a.med_out = med[li ^ 1];
+        a.chunk_out = chunk[li ^ 1];
+        a.acc = acc;
+        a.st = st;
+        a.hub_deg = hub;
+        const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
+        if (dt.n_cls == 0) k_lcc_round<0><<<g, 256, 0, s>>>(a, dt);
+        else if (dt.n_cls <= 4) k_lcc_round<4><<<g, 256, 0, s>>>(a, dt);
+        else k_lcc_round<32><<<g, 256, 0, s>>>(a, dt);
+        NA_CU(cudaGetLastError());
+        NA_CU(read_stats());
+        r++;
+        scanned += (int64_t)hs.scanned;
+        n_small = hs.n_small;
+        n_med = hs.n_med;
+        n_chunk = hs.n_chunk;
+        li ^= 1;
+        cur ^= 1;
+        if (!hs.changed) break;
+        if (r > 4 * (m_dir + n) + 8) return fail(CCPM_ETIMEOUT, "LCC did not converge");
+    }
+    // both omega buffers agree at the fixpoint; the caller's buffer must hold it
+    if (cur != 0) NA_CU(cudaMemcpyAsync(omega, om[cur], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (m_dir > 0) {
+        k_materialize<<<grid(n * 32, 256), 256, 0, s>>>(n, omega, row_ptr, col, ebits);
+        NA_CU(cudaGetLastError());
+    }
+    NA_CU(cudaStreamSynchronize(s));
+#undef NA_CU
+    if (rounds) *rounds = r;
+    if (edges_scanned) *edges_scanned = scanned;
+    return CCPM_OK;
+}
