@@ -44,6 +44,7 @@ struct RoundStats {
     unsigned int n_small, n_med, n_chunk;   // next frontier sizes
     unsigned int n_hub_slots;
     unsigned int n_roots;
+    unsigned int n_items;         // (root, head, first candidate) search items
     unsigned int overflow;        // a search hit its budget
     unsigned int pad;
 };
@@ -84,6 +85,7 @@ struct WarpBuf {
     int *cnt;        // shared counter
     T *out;          // global list
     unsigned int *gcount;
+    unsigned long long cap = ~0ull;   // items past this index are counted, not stored
 
     __device__ __forceinline__ void flush() {
         int c = *cnt;
@@ -91,7 +93,7 @@ struct WarpBuf {
         unsigned int base = 0;
         if (lane_id() == 0) base = atomicAdd(gcount, (unsigned int)c);
         base = __shfl_sync(FULL_MASK, base, 0);
-        if ((int)lane_id() < c) out[base + lane_id()] = buf[lane_id()];
+        if ((int)lane_id() < c && (unsigned long long)base + lane_id() < cap) out[base + lane_id()] = buf[lane_id()];
         __syncwarp();
         if (lane_id() == 0) *cnt = 0;
         __syncwarp();
@@ -465,7 +467,13 @@ struct SearchArgs {
     RoundStats *st;
     uint64_t budget;          // windows per (root, head)
     uint64_t cap;             // final: stop past this many matches
+    int4 *items;              // (root, first candidate, head, -) split search work
+    int64_t n_items;
+    int64_t items_cap;
+    int enum_heads;           // k_expand: 1 = final search (one head), 0 = NLCC
 };
+
+constexpr int kMaxBack = 4;  // joins per level whose label group is kept in shared memory
 
 struct WarpSearch {
     int32_t psi[kMaxT];
@@ -473,7 +481,9 @@ struct WarpSearch {
     int64_t end[kMaxT];
     int64_t wbase[kMaxT];     // start of the window the mask refers to
     uint32_t mask[kMaxT];     // untried valid candidates of that window
-    uint32_t chk[kMaxT];      // placed neighbours still to be tested by lookup
+    uint32_t chk[kMaxT];      // further joins, looked up from scratch per candidate
+    int nb[kMaxT];            // joins with a stored label group
+    int64_t blo[kMaxT][kMaxBack], bhi[kMaxT][kMaxBack];
 };
 
 // [lo, hi) of the label-L group in the label-grouped row of x.
@@ -538,14 +548,20 @@ __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P
         int ob = __shfl_xor_sync(FULL_MASK, best, o);
         if (ol < len || (ol == len && ob < best)) { len = ol; best = ob; }
     }
-    lo = __shfl_sync(FULL_MASK, lo, best);
-    hi = __shfl_sync(FULL_MASK, hi, best);
-    j = __shfl_sync(FULL_MASK, j, best);
-    if (lane == 0) {
+    // the other placed neighbours are joins: keep their label groups
+    const int slot = lane < best ? lane : lane - 1;
+    const bool join = lane < cnt && lane != best;
+    if (join && slot < kMaxBack) {
+        W.blo[d][slot] = lo;
+        W.bhi[d][slot] = hi;
+    }
+    const uint32_t extra = __reduce_or_sync(FULL_MASK, (join && slot >= kMaxBack) ? (1u << j) : 0u);
+    if (lane == best) {
         W.pos[d] = lo;
         W.end[d] = hi;
         W.mask[d] = 0u;
-        W.chk[d] = cm & ~(1u << j);
+        W.chk[d] = extra;
+        W.nb[d] = min(cnt - 1, kMaxBack);
     }
     __syncwarp();
 }
@@ -555,35 +571,78 @@ __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P
 // budget ran out; for existence the root is then reported as satisfied, which
 // keeps the result a superset of the exact answer.
 template <bool ENUM>
-__device__ bool search_root(const SearchArgs &a, const DevPlan &P, int32_t root, WarpSearch &W,
+__device__ __forceinline__ void mark_match(const SearchArgs &a, const DevPlan &P, WarpSearch &W) {
+    const int lane = (int)lane_id();
+    if (lane < P.k) {
+        int32_t x = W.psi[lane];
+        uint32_t bit = 1u << P.q[lane];
+        if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
+    }
+    for (int t = lane; t < P.n_marks; t += 32) {
+        int32_t x = W.psi[P.mark_a[t]], y = W.psi[P.mark_b[t]];
+        int64_t e1 = find_entry(a.rp, a.col, x, y);
+        int64_t e2 = find_entry(a.rp, a.col, y, x);
+        if (e1 >= 0) {
+            uint32_t b1 = 1u << (uint32_t)(e1 & 31);
+            if (!(a.eb_out[e1 >> 5] & b1)) atomicOr(&a.eb_out[e1 >> 5], b1);
+        }
+        if (e2 >= 0) {
+            uint32_t b2 = 1u << (uint32_t)(e2 & 31);
+            if (!(a.eb_out[e2 >> 5] & b2)) atomicOr(&a.eb_out[e2 >> 5], b2);
+        }
+    }
+    __syncwarp();
+}
+
+// Is the entry e of the scanned label group a valid image u for position d?
+// Its omega must hold q_d, it must differ from earlier same-label images, and
+// it must be joined to every other placed neighbour of position d.
+__device__ __forceinline__ bool test_candidate(const SearchArgs &a, const DevPlan &P, const WarpSearch &W,
+                                               int d, int64_t e, int64_t end, int32_t &u) {
+    u = -1;
+    if (e >= end) return false;
+    u = __ldg(a.lcol + e);
+    if (!((__ldg(a.om + u) >> P.q[d]) & 1u)) return false;
+    for (uint32_t sm = P.same[d]; sm; sm &= sm - 1u)
+        if (W.psi[__ffs(sm) - 1] == u) return false;
+    for (int b = 0; b < W.nb[d]; b++) {
+        int64_t lo = W.blo[d][b], hi = W.bhi[d][b];
+        const int64_t stop = hi;
+        while (lo < hi) {
+            int64_t m2 = (lo + hi) >> 1;
+            if (__ldg(a.lcol + m2) < u) lo = m2 + 1; else hi = m2;
+        }
+        if (!(lo < stop && __ldg(a.lcol + lo) == u)) return false;
+    }
+    for (uint32_t bm = W.chk[d]; bm; bm &= bm - 1u)
+        if (!adjacent(a, W.psi[__ffs(bm) - 1], u, P.lab[d])) return false;
+    return true;
+}
+
+// Depth-first search from positions 0..d0-1 already placed in W.psi.
+template <bool ENUM>
+__device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpSearch &W,
                             unsigned long long &entries, unsigned long long &matches, bool &over) {
     const int lane = (int)lane_id();
     const int k = P.k;
     uint64_t used = 0;
-    if (lane == 0) W.psi[0] = root;
-    __syncwarp();
-    open_level(a, P, W, 1);
-    int d = 1;
-    while (d >= 1) {
+    if (d0 >= k) {                                  // the placed prefix is already a full map
+        if (!ENUM) return true;
+        matches++;
+        mark_match<ENUM>(a, P, W);
+        return false;
+    }
+    open_level(a, P, W, d0);
+    int d = d0;
+    while (d >= d0) {
         const uint32_t m = W.mask[d];
         if (m == 0u) {
             const int64_t pos = W.pos[d], end = W.end[d];
             if (pos >= end) { d--; continue; }
             if (++used > a.budget) { over = true; return !ENUM; }
             entries += (unsigned long long)min((int64_t)32, end - pos);
-            const int64_t e = pos + lane;
-            const int q = P.q[d];
-            bool ok = false;
-            if (e < end) {
-                const int32_t u = __ldg(a.lcol + e);
-                if ((__ldg(a.om + u) >> q) & 1u) {
-                    ok = true;
-                    for (uint32_t sm = P.same[d]; sm && ok; sm &= sm - 1u)
-                        if (W.psi[__ffs(sm) - 1] == u) ok = false;
-                    for (uint32_t bm = W.chk[d]; bm && ok; bm &= bm - 1u)
-                        ok = adjacent(a, W.psi[__ffs(bm) - 1], u, P.lab[d]);
-                }
-            }
+            int32_t u;
+            const bool ok = test_candidate(a, P, W, d, pos + lane, end, u);
             const uint32_t vm = __ballot_sync(FULL_MASK, ok);
             if (lane == 0) { W.mask[d] = vm; W.wbase[d] = pos; W.pos[d] = pos + 32; }
             __syncwarp();
@@ -597,25 +656,7 @@ __device__ bool search_root(const SearchArgs &a, const DevPlan &P, int32_t root,
             matches++;
             // mark the match: omega*(psi(i)) gets q_i, both directions of
             // every template edge get their bit (id-sorted entry indices)
-            if (lane < k) {
-                int32_t x = W.psi[lane];
-                uint32_t bit = 1u << P.q[lane];
-                if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
-            }
-            for (int t = lane; t < P.n_marks; t += 32) {
-                int32_t x = W.psi[P.mark_a[t]], y = W.psi[P.mark_b[t]];
-                int64_t e1 = find_entry(a.rp, a.col, x, y);
-                int64_t e2 = find_entry(a.rp, a.col, y, x);
-                if (e1 >= 0) {
-                    uint32_t b1 = 1u << (uint32_t)(e1 & 31);
-                    if (!(a.eb_out[e1 >> 5] & b1)) atomicOr(&a.eb_out[e1 >> 5], b1);
-                }
-                if (e2 >= 0) {
-                    uint32_t b2 = 1u << (uint32_t)(e2 & 31);
-                    if (!(a.eb_out[e2 >> 5] & b2)) atomicOr(&a.eb_out[e2 >> 5], b2);
-                }
-            }
-            __syncwarp();
+            mark_match<ENUM>(a, P, W);
             continue;
         }
         d++;
@@ -636,16 +677,17 @@ k_nlcc_search(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
-    unsigned long long entries = 0, matches = 0, tokens = 0;
+    unsigned long long entries = 0, matches = 0;
     bool over = false;
     for (int64_t it = grab_root(a); it < a.n_roots; it = grab_root(a)) {
         const int32_t v = a.roots[it];
         const uint32_t hv = __ldg(a.om + v) & a.heads;
-        tokens += (unsigned long long)__popc(hv);
         uint32_t sat = 0;
         for (uint32_t hm = hv; hm; hm &= hm - 1u) {
             const int h = __ffs(hm) - 1;
-            if (search_root<false>(a, a.plans[h], v, W, entries, matches, over)) sat |= 1u << h;
+            if (lane == 0) W.psi[0] = v;
+            __syncwarp();
+            if (search_from<false>(a, a.plans[h], 1, W, entries, matches, over)) sat |= 1u << h;
             __syncwarp();
         }
         if (lane == 0) a.sat[v] = sat;
@@ -653,7 +695,6 @@ k_nlcc_search(SearchArgs a) {
     // entries, tokens and over are identical in every lane of the warp
     if (lane == 0) {
         if (entries) atomicAdd(&a.st->windows, entries);
-        if (tokens) atomicAdd(&a.st->tokens, tokens);
         if (over) atomicOr(&a.st->overflow, 1u);
     }
 }
@@ -672,8 +713,172 @@ k_final_search(SearchArgs a) {
         if (__shfl_sync(FULL_MASK, stop, 0)) break;
         const int32_t v = a.roots[it];
         unsigned long long before = matches;
-        search_root<true>(a, a.plans[0], v, W, entries, matches, over);
+        if (lane == 0) W.psi[0] = v;
         __syncwarp();
+        search_from<true>(a, a.plans[0], 1, W, entries, matches, over);
+        __syncwarp();
+        if (matches != before) {
+            unsigned long long tot = 0;
+            if (lane == 0) tot = atomicAdd(&a.st->matches, matches - before) + (matches - before);
+            tot = __shfl_sync(FULL_MASK, tot, 0);
+            if (tot > a.cap) over = true;
+        }
+        if (over) {
+            if (lane == 0) atomicOr(&a.st->overflow, 1u);
+            break;
+        }
+    }
+    if (lane == 0 && entries) atomicAdd(&a.st->windows, entries);
+}
+
+// Split search work by the first level: every (root, head) becomes one item per
+// candidate for position 1, so expensive roots spread over many warps.
+__global__ void __launch_bounds__(256)
+k_expand(SearchArgs a) {
+    __shared__ int4 sbuf[8][32];
+    __shared__ int scnt[8];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    if (lane == 0) scnt[wib] = 0;
+    __syncthreads();
+    WarpBuf<int4> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
+    b.cap = (unsigned long long)a.items_cap;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long entries = 0, tokens = 0;
+    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+        const int32_t v = a.roots[it];
+        const uint32_t hv = a.enum_heads ? a.heads : (__ldg(a.om + v) & a.heads);
+        if (!a.enum_heads && lane == 0) a.sat[v] = 0u;
+        tokens += (unsigned long long)__popc(hv);
+        for (uint32_t hm = hv; hm; hm &= hm - 1u) {
+            const int h = __ffs(hm) - 1;
+            const DevPlan &P = a.plans[a.enum_heads ? 0 : h];
+            const int q1 = P.q[1];
+            int64_t lo, hi;
+            label_range(a.rp, a.nlab, v, P.lab[1], lo, hi);
+            entries += (unsigned long long)(hi - lo);
+            for (int64_t base = lo; base < hi; base += 32) {
+                const int64_t e = base + lane;
+                bool ok = false;
+                int32_t u = -1;
+                if (e < hi) {
+                    u = __ldg(a.lcol + e);
+                    ok = ((__ldg(a.om + u) >> q1) & 1u) && !((P.same[1] & 1u) && u == v);
+                }
+                b.push(ok, make_int4(v, u, 0, h | (2 << 8)));
+            }
+        }
+    }
+    b.flush();
+    if (lane == 0) {
+        if (entries) atomicAdd(&a.st->windows, entries);
+        if (tokens) atomicAdd(&a.st->tokens, tokens);
+    }
+}
+
+// When the first level gives too few items to fill the GPU, place position 2
+// as well: each input item (root, first, head) becomes one item per valid
+// image of position 2.  Items whose plan has no position 2 pass through.
+__global__ void __launch_bounds__(128)
+k_expand2(SearchArgs a, const int4 *in, int64_t n_in) {
+    __shared__ WarpSearch ws[4];
+    __shared__ int4 sbuf[4][32];
+    __shared__ int scnt[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    if (lane == 0) scnt[wib] = 0;
+    __syncthreads();
+    WarpBuf<int4> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
+    b.cap = (unsigned long long)a.items_cap;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long entries = 0;
+    for (int64_t it = gwarp; it < n_in; it += nwarps) {
+        const int4 item = in[it];
+        const int h = item.w & 0xff;
+        const DevPlan &P = a.plans[a.enum_heads ? 0 : h];
+        if (P.k <= 2) {
+            b.push(lane == 0, item);
+            continue;
+        }
+        if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; }
+        __syncwarp();
+        open_level(a, P, W, 2);
+        const int64_t lo = W.pos[2], hi = W.end[2];
+        entries += (unsigned long long)(hi - lo);
+        for (int64_t base = lo; base < hi; base += 32) {
+            int32_t u;
+            const bool ok = test_candidate(a, P, W, 2, base + lane, hi, u);
+            b.push(ok, make_int4(item.x, item.y, u, h | (3 << 8)));
+        }
+    }
+    b.flush();
+    if (lane == 0 && entries) atomicAdd(&a.st->windows, entries);
+}
+
+__device__ __forceinline__ int64_t grab_items(const SearchArgs &a, int batch) {
+    unsigned long long r = 0;
+    if (lane_id() == 0) r = atomicAdd(a.next_root, (unsigned long long)batch);
+    return (int64_t)__shfl_sync(FULL_MASK, r, 0);
+}
+
+constexpr int kItemBatch = 4;
+// Below this many first-level items the searches place position 2 as well.
+constexpr int64_t kExpandBelow = 16384;
+
+__global__ void __launch_bounds__(128)
+k_nlcc_items(SearchArgs a) {
+    __shared__ WarpSearch ws[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    unsigned long long entries = 0, matches = 0;
+    bool over = false;
+    for (int64_t it0 = grab_items(a, kItemBatch); it0 < a.n_items; it0 = grab_items(a, kItemBatch)) {
+        const int64_t it1 = min(a.n_items, it0 + kItemBatch);
+        for (int64_t it = it0; it < it1; it++) {
+            const int4 item = a.items[it];
+            const int h = item.w & 0xff, depth = item.w >> 8;
+            const uint32_t bit = 1u << h;
+            uint32_t done = 0;                                       // satisfied by another item?
+            if (lane == 0) done = *(volatile uint32_t *)&a.sat[item.x] & bit;
+            if (__shfl_sync(FULL_MASK, done, 0)) continue;
+            if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; W.psi[2] = item.z; }
+            __syncwarp();
+            if (search_from<false>(a, a.plans[h], depth, W, entries, matches, over) && lane == 0)
+                atomicOr(&a.sat[item.x], bit);
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        if (entries) atomicAdd(&a.st->windows, entries);
+        if (over) atomicOr(&a.st->overflow, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(128)
+k_final_items(SearchArgs a) {
+    __shared__ WarpSearch ws[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    unsigned long long entries = 0, matches = 0;
+    bool over = false;
+    for (int64_t it0 = grab_items(a, kItemBatch); it0 < a.n_items; it0 = grab_items(a, kItemBatch)) {
+        unsigned int stop = 0;
+        if (lane == 0) stop = *(volatile unsigned int *)&a.st->overflow;
+        if (__shfl_sync(FULL_MASK, stop, 0)) break;
+        const int64_t it1 = min(a.n_items, it0 + kItemBatch);
+        const unsigned long long before = matches;
+        for (int64_t it = it0; it < it1 && !over; it++) {
+            const int4 item = a.items[it];
+            if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; W.psi[2] = item.z; }
+            __syncwarp();
+            search_from<true>(a, a.plans[0], item.w >> 8, W, entries, matches, over);
+            __syncwarp();
+        }
         if (matches != before) {
             unsigned long long tot = 0;
             if (lane == 0) tot = atomicAdd(&a.st->matches, matches - before) + (matches - before);
@@ -813,6 +1018,9 @@ struct Workspace {
     int64_t acc_cap = 0;
     int32_t *roots = nullptr;
     uint32_t *sat = nullptr;
+    int4 *items = nullptr;           // split search work
+    int64_t items_cap = 0;
+    int4 *items2 = nullptr;          // input of the second-level expansion
     DevPlan *plans = nullptr;
     RoundStats *st = nullptr;        // device
     unsigned long long *next_root = nullptr;   // dynamic root counter of the searches
@@ -880,7 +1088,7 @@ void ws_free(Workspace &w) {
     cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.ebits);
     cudaFree(w.small[0]); cudaFree(w.small[1]); cudaFree(w.med[0]); cudaFree(w.med[1]);
     cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
-    cudaFree(w.sat); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
+    cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
     if (w.st_h) cudaFreeHost(w.st_h);
     if (w.cnt_h) cudaFreeHost(w.cnt_h);
     if (w.plans_h) cudaFreeHost(w.plans_h);
@@ -910,6 +1118,9 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     if ((rc = dalloc(ctx, &w.acc, (size_t)w.acc_cap))) return rc;
     if ((rc = dalloc(ctx, &w.roots, (size_t)g->n))) return rc;
     if ((rc = dalloc(ctx, &w.sat, (size_t)g->n))) return rc;
+    w.items_cap = std::min<int64_t>(std::max<int64_t>(g->m, (int64_t)1 << 22), (int64_t)1 << 25);
+    if ((rc = dalloc(ctx, &w.items, (size_t)w.items_cap))) return rc;
+    if ((rc = dalloc(ctx, &w.items2, (size_t)kExpandBelow))) return rc;
     if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxT))) return rc;
     if ((rc = dalloc(ctx, &w.st, 1))) return rc;
     if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
@@ -952,6 +1163,32 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
                        std::string("label-grouped rows: ") + cudaGetErrorString(e));
     }
     return CCPM_OK;
+}
+
+// Split search work one level deeper when there is too little of it.
+int expand_more(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int64_t &launches) {
+    if (a.n_items <= 0 || a.n_items >= kExpandBelow) return CCPM_OK;
+    CU(ctx, cudaMemcpyAsync(w.items2, w.items, sizeof(int4) * (size_t)a.n_items, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(ctx, cudaMemsetAsync(&w.st->n_items, 0, sizeof(unsigned int), ctx->stream));
+    launches++;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_items + 3) / 4, (int64_t)ctx->num_sms * 16));
+    k_expand2<<<grid, 128, 0, ctx->stream>>>(a, w.items2, a.n_items);
+    CU(ctx, cudaGetLastError());
+    unsigned int n2 = 0;
+    CU(ctx, cudaMemcpyAsync(&n2, &w.st->n_items, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    a.n_items = n2;
+    return CCPM_OK;
+}
+
+// Grid of one resident wave for a 256-thread grid-stride kernel.
+template <typename K>
+int lcc_grid(ccpm_ctx *ctx, K kernel, int64_t warps) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 4;
+    int64_t need = (warps + 7) / 8;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)ctx->num_sms * per_sm));
 }
 
 int grid_for(ccpm_ctx *ctx, int64_t work_items, int per_block, int blocks_per_sm) {
@@ -1003,12 +1240,12 @@ struct Pipeline {
         a.st = w.st;
         a.hub_deg = w.hub_deg;
         int64_t warps = n_chunk + n_med + (n_small + 7) / 8;
-        int grid = grid_for(ctx, warps * 32, 256, 8);
         launches++;
         lcc_launches++;
-        if (maxc == 0) k_lcc_round<0><<<grid, 256, 0, ctx->stream>>>(a, dt);
-        else if (maxc <= 4) k_lcc_round<4><<<grid, 256, 0, ctx->stream>>>(a, dt);
-        else k_lcc_round<32><<<grid, 256, 0, ctx->stream>>>(a, dt);
+        // one resident wave: grid-stride work is split evenly over warps that all run at once
+        if (maxc == 0) k_lcc_round<0><<<lcc_grid(ctx, k_lcc_round<0>, warps), 256, 0, ctx->stream>>>(a, dt);
+        else if (maxc <= 4) k_lcc_round<4><<<lcc_grid(ctx, k_lcc_round<4>, warps), 256, 0, ctx->stream>>>(a, dt);
+        else k_lcc_round<32><<<lcc_grid(ctx, k_lcc_round<32>, warps), 256, 0, ctx->stream>>>(a, dt);
         CU(ctx, cudaGetLastError());
         return CCPM_OK;
     }
@@ -1365,8 +1602,23 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.sat = w.sat;
             a.st = w.st;
             a.budget = budget;
+            a.items = w.items;
+            a.items_cap = w.items_cap;
+            a.enum_heads = 0;
+            // one item per (root, head, candidate for position 1)
             P.launches++;
-            k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            k_expand<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a);
+            CUF(cudaGetLastError());
+            RCF(P.read_stats());
+            a.n_items = w.st_h->n_items;
+            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, P.launches));
+            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+            P.launches++;
+            if (a.n_items <= w.items_cap) {
+                k_nlcc_items<<<grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16), 128, 0, s>>>(a);
+            } else {
+                k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            }
             CUF(cudaGetLastError());
             P.launches++;
             k_nlcc_apply<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, c.hmask, w.sat,
@@ -1427,8 +1679,22 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.st = w.st;
             a.budget = budget;
             a.cap = opt.max_embeddings;
+            a.items = w.items;
+            a.items_cap = w.items_cap;
+            a.enum_heads = 1;
             P.launches++;
-            k_final_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            k_expand<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a);
+            CUF(cudaGetLastError());
+            RCF(P.read_stats());
+            a.n_items = w.st_h->n_items;
+            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, P.launches));
+            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+            P.launches++;
+            if (a.n_items <= w.items_cap) {
+                k_final_items<<<grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16), 128, 0, s>>>(a);
+            } else {
+                k_final_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            }
             CUF(cudaGetLastError());
             RCF(P.read_stats());
         }
