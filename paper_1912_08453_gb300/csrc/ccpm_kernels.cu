@@ -221,55 +221,126 @@ struct Partial {
     }
 };
 
-// Stream the CSR entries [beg, end) of an active vertex with G lanes: edge
-// elimination by eta (entry kept iff the neighbour's omega contains a template
-// neighbour of some q in omega(v)), the union omega' of Alg. 4 and the
-// per-class counts of distinct compatible neighbours.
-template <int G, int MAXC>
-__device__ __forceinline__ void scan_entries(int64_t beg, int64_t end, uint32_t nbr_v, int lane_g,
-                                             const int32_t *__restrict__ col,
-                                             const uint32_t *__restrict__ om, uint32_t *ebits,
-                                             const SmemTmpl &s, Partial<MAXC> &p,
-                                             unsigned long long &scanned) {
-    constexpr int UNR = G >= 32 ? 8 : 4;   // entries in flight per lane
-    for (int64_t base = beg + lane_g; base < end; base += (int64_t)G * UNR) {
+// Stream the CSR entries [beg, end) of an active vertex: edge elimination by
+// eta (entry kept iff the neighbour's omega contains a template neighbour of
+// some q in omega(v)), the union omega' of Alg. 4 and the per-class counts of
+// distinct compatible neighbours.
+//
+// Warp form: all 32 lanes walk the row together, window by window (32
+// consecutive entries per window), so failing entries of a window are
+// cleared with one ballot and at most two atomics.
+// DENSE: every edge bit of the rows read is still set (the first round after
+// init), so the bits are not loaded; otherwise a column index is only loaded
+// for entries whose bit is set.
+template <int MAXC, bool DENSE>
+__device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t nbr_v,
+                                              const int32_t *__restrict__ col,
+                                              const uint32_t *__restrict__ om, uint32_t *ebits,
+                                              const SmemTmpl &s, Partial<MAXC> &p,
+                                              unsigned long long &scanned) {
+    constexpr int UNR = 8;   // windows in flight
+    const int lane = (int)lane_id();
+    for (int64_t base = beg; base < end; base += 32 * UNR) {
         uint32_t word[UNR];
         int32_t u[UNR];
+        bool act[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            int64_t e = base + (int64_t)j * G;
-            word[j] = 0u;
-            u[j] = 0;
-            if (e < end) {
-                word[j] = ebits[e >> 5];
-                u[j] = __ldg(col + e);
-            }
+            const int64_t e = base + j * 32 + lane;
+            word[j] = DENSE ? ~0u : 0u;
+            if (!DENSE && e < end) word[j] = ebits[e >> 5];
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            const int64_t e = base + j * 32 + lane;
+            act[j] = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
+            u[j] = act[j] ? __ldg(col + e) : 0;
         }
         uint32_t wu[UNR];
 #pragma unroll
-        for (int j = 0; j < UNR; j++) {
-            int64_t e = base + (int64_t)j * G;
-            bool act = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
-            wu[j] = act ? __ldg(om + u[j]) : 0u;
-        }
+        for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            uint32_t w = wu[j];
-            if (!w) continue;
-            scanned++;
-            if (w & nbr_v) {
-                p.U |= w;
-                p.nN++;
+            const uint32_t w = wu[j];
+            bool fail = false;
+            if (w) {
+                scanned++;
+                if (w & nbr_v) {
+                    p.U |= w;
+                    p.nN++;
 #pragma unroll
-                for (int c = 0; c < MAXC; c++)
-                    if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
-            } else {
-                int64_t e = base + (int64_t)j * G;
-                atomicAnd(&ebits[e >> 5], ~(1u << (uint32_t)(e & 31)));
+                    for (int c = 0; c < MAXC; c++)
+                        if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
+                } else {
+                    fail = true;
+                }
+            }
+            const uint32_t clr = __ballot_sync(FULL_MASK, fail);
+            if (clr) {
                 p.achg = 1u;
+                if (lane == 0) {
+                    const int64_t e0 = base + j * 32;
+                    const uint32_t sh = (uint32_t)(e0 & 31);
+                    atomicAnd(&ebits[e0 >> 5], ~(clr << sh));
+                    if (sh && (clr >> (32 - sh))) atomicAnd(&ebits[(e0 >> 5) + 1], ~(clr >> (32 - sh)));
+                }
             }
         }
     }
+}
+
+// Group form for rows of at most 32 entries: G lanes share a row; failing
+// entries are collected as a row-relative mask and cleared once per row.
+template <int G, int MAXC, bool DENSE>
+__device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uint32_t nbr_v, int lane_g,
+                                                   const int32_t *__restrict__ col,
+                                                   const uint32_t *__restrict__ om, const uint32_t *ebits,
+                                                   const SmemTmpl &s, Partial<MAXC> &p,
+                                                   unsigned long long &scanned) {
+    constexpr int UNR = 32 / G;   // covers the whole row in one pass
+    uint32_t word[UNR];
+    int32_t u[UNR];
+    bool act[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; j++) {
+        const int64_t e = beg + lane_g + j * G;
+        word[j] = DENSE ? ~0u : 0u;
+        if (!DENSE && e < end) word[j] = ebits[e >> 5];
+    }
+#pragma unroll
+    for (int j = 0; j < UNR; j++) {
+        const int64_t e = beg + lane_g + j * G;
+        act[j] = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
+        u[j] = act[j] ? __ldg(col + e) : 0;
+    }
+    uint32_t wu[UNR];
+#pragma unroll
+    for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+    uint32_t clr = 0u;
+#pragma unroll
+    for (int j = 0; j < UNR; j++) {
+        const uint32_t w = wu[j];
+        if (!w) continue;
+        scanned++;
+        if (w & nbr_v) {
+            p.U |= w;
+            p.nN++;
+#pragma unroll
+            for (int c = 0; c < MAXC; c++)
+                if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
+        } else {
+            clr |= 1u << (uint32_t)(lane_g + j * G);
+        }
+    }
+    return clr;
+}
+
+// Clear the entries of a row (at most 32 long) given by a row-relative mask.
+__device__ __forceinline__ void clear_rel(uint32_t *ebits, int64_t beg, uint32_t clr) {
+    if (!clr) return;
+    const uint32_t sh = (uint32_t)(beg & 31);
+    atomicAnd(&ebits[beg >> 5], ~(clr << sh));
+    if (sh && (clr >> (32 - sh))) atomicAnd(&ebits[(beg >> 5) + 1], ~(clr >> (32 - sh)));
 }
 
 // The vertex-elimination rule of Alg. 4 plus the multiplicity rule of
@@ -295,7 +366,7 @@ __device__ __forceinline__ uint32_t nbr_mask(uint32_t wv, const SmemTmpl &s) {
     return m;
 }
 
-template <int MAXC>
+template <int MAXC, bool DENSE>
 __global__ void __launch_bounds__(256)
 k_lcc_round(LccArgs a, DevTmpl t) {
     __shared__ SmemTmpl s;
@@ -329,7 +400,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
         if (lane == 0) { rows += (unsigned long long)(end - beg); alive += ci.c == 0; }
         Partial<MAXC> p;
-        scan_entries<32, MAXC>(beg, end, nbr_mask(wv, s), lane, a.col, a.om_cur, a.ebits, s, p, scanned);
+        scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -378,7 +449,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             const int64_t beg = a.rp[v], end = a.rp[v + 1];
             if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
             Partial<MAXC> p;
-            scan_entries<32, MAXC>(beg, end, nbr_mask(wv, s), lane, a.col, a.om_cur, a.ebits, s, p, scanned);
+            scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
             p.U = grp_or<32>(p.U);
             p.nN = grp_sum<32>(p.nN);
             p.achg = grp_or<32>(p.achg);
@@ -403,7 +474,11 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         if (wv) { beg = a.rp[v]; end = a.rp[v + 1]; }
         if (lg == 0 && wv) { rows += (unsigned long long)(end - beg); alive++; }
         Partial<MAXC> p;
-        scan_entries<4, MAXC>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits, s, p, scanned);
+        uint32_t clr = scan_row_group<4, MAXC, DENSE>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits, s, p,
+                                               scanned);
+        clr = grp_or<4>(clr);
+        p.achg = clr ? 1u : 0u;
+        if (lg == 0 && wv) clear_rel(a.ebits, beg, clr);
         p.U = grp_or<4>(p.U);
         p.nN = grp_sum<4>(p.nN);
         p.achg = grp_or<4>(p.achg);
@@ -450,6 +525,13 @@ k_lcc_round(LccArgs a, DevTmpl t) {
 // neighbours that carry label(q) are ever scanned.
 // -------------------------------------------------------------------------
 
+// A partial embedding of a search plan: positions 0..depth-1 placed.
+constexpr int kItemMaxDepth = 7;
+struct __align__(16) SearchItem {
+    int32_t psi[kItemMaxDepth];
+    int32_t hd;               // head | depth << 8
+};
+
 struct SearchArgs {
     const int64_t *rp;
     const int32_t *col;       // id-sorted rows (edge-bitmap indexing)
@@ -467,7 +549,7 @@ struct SearchArgs {
     RoundStats *st;
     uint64_t budget;          // windows per (root, head)
     uint64_t cap;             // final: stop past this many matches
-    int4 *items;              // (root, first candidate, head, -) split search work
+    SearchItem *items;        // split search work: partial embeddings
     int64_t n_items;
     int64_t items_cap;
     int enum_heads;           // k_expand: 1 = final search (one head), 0 = NLCC
@@ -735,13 +817,13 @@ k_final_search(SearchArgs a) {
 // candidate for position 1, so expensive roots spread over many warps.
 __global__ void __launch_bounds__(256)
 k_expand(SearchArgs a) {
-    __shared__ int4 sbuf[8][32];
+    __shared__ SearchItem sbuf[8][32];
     __shared__ int scnt[8];
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     if (lane == 0) scnt[wib] = 0;
     __syncthreads();
-    WarpBuf<int4> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
+    WarpBuf<SearchItem> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
     b.cap = (unsigned long long)a.items_cap;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -766,7 +848,11 @@ k_expand(SearchArgs a) {
                     u = __ldg(a.lcol + e);
                     ok = ((__ldg(a.om + u) >> q1) & 1u) && !((P.same[1] & 1u) && u == v);
                 }
-                b.push(ok, make_int4(v, u, 0, h | (2 << 8)));
+                SearchItem si;
+                si.psi[0] = v;
+                si.psi[1] = u;
+                si.hd = h | (2 << 8);
+                b.push(ok, si);
             }
         }
     }
@@ -777,41 +863,44 @@ k_expand(SearchArgs a) {
     }
 }
 
-// When the first level gives too few items to fill the GPU, place position 2
-// as well: each input item (root, first, head) becomes one item per valid
-// image of position 2.  Items whose plan has no position 2 pass through.
+// When there are too few items to fill the GPU, place one more position:
+// every input item of depth D becomes one item per valid image of position D.
+// Items that already place every position pass through.
 __global__ void __launch_bounds__(128)
-k_expand2(SearchArgs a, const int4 *in, int64_t n_in) {
+k_expand_next(SearchArgs a, const SearchItem *in, int64_t n_in) {
     __shared__ WarpSearch ws[4];
-    __shared__ int4 sbuf[4][32];
+    __shared__ SearchItem sbuf[4][32];
     __shared__ int scnt[4];
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
     if (lane == 0) scnt[wib] = 0;
     __syncthreads();
-    WarpBuf<int4> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
+    WarpBuf<SearchItem> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
     b.cap = (unsigned long long)a.items_cap;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long entries = 0;
     for (int64_t it = gwarp; it < n_in; it += nwarps) {
-        const int4 item = in[it];
-        const int h = item.w & 0xff;
+        const SearchItem item = in[it];
+        const int h = item.hd & 0xff, depth = item.hd >> 8;
         const DevPlan &P = a.plans[a.enum_heads ? 0 : h];
-        if (P.k <= 2) {
+        if (depth >= P.k || depth >= kItemMaxDepth) {
             b.push(lane == 0, item);
             continue;
         }
-        if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; }
+        if (lane < depth) W.psi[lane] = item.psi[lane];
         __syncwarp();
-        open_level(a, P, W, 2);
-        const int64_t lo = W.pos[2], hi = W.end[2];
+        open_level(a, P, W, depth);
+        const int64_t lo = W.pos[depth], hi = W.end[depth];
         entries += (unsigned long long)(hi - lo);
         for (int64_t base = lo; base < hi; base += 32) {
             int32_t u;
-            const bool ok = test_candidate(a, P, W, 2, base + lane, hi, u);
-            b.push(ok, make_int4(item.x, item.y, u, h | (3 << 8)));
+            const bool ok = test_candidate(a, P, W, depth, base + lane, hi, u);
+            SearchItem si = item;
+            si.psi[depth] = u;
+            si.hd = h | ((depth + 1) << 8);
+            b.push(ok, si);
         }
     }
     b.flush();
@@ -839,16 +928,27 @@ k_nlcc_items(SearchArgs a) {
     for (int64_t it0 = grab_items(a, kItemBatch); it0 < a.n_items; it0 = grab_items(a, kItemBatch)) {
         const int64_t it1 = min(a.n_items, it0 + kItemBatch);
         for (int64_t it = it0; it < it1; it++) {
-            const int4 item = a.items[it];
-            const int h = item.w & 0xff, depth = item.w >> 8;
+            const SearchItem item = a.items[it];
+            const int h = item.hd & 0xff, depth = item.hd >> 8;
             const uint32_t bit = 1u << h;
             uint32_t done = 0;                                       // satisfied by another item?
-            if (lane == 0) done = *(volatile uint32_t *)&a.sat[item.x] & bit;
+            if (lane == 0) done = *(volatile uint32_t *)&a.sat[item.psi[0]] & bit;
             if (__shfl_sync(FULL_MASK, done, 0)) continue;
-            if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; W.psi[2] = item.z; }
+            if (lane < depth) W.psi[lane] = item.psi[lane];
             __syncwarp();
-            if (search_from<false>(a, a.plans[h], depth, W, entries, matches, over) && lane == 0)
-                atomicOr(&a.sat[item.x], bit);
+            bool ran_out = false;
+            if (search_from<false>(a, a.plans[h], depth, W, entries, matches, ran_out)) {
+                const DevPlan &P = a.plans[h];
+                if (ran_out) {
+                    // budget exhausted: keep the head (a superset of the exact answer)
+                    if (lane == 0) atomicOr(&a.sat[item.psi[0]], bit);
+                } else if (lane < P.k) {
+                    // the embedding found satisfies every head it places, not only h
+                    const int q = P.q[lane];
+                    if ((a.heads >> q) & 1u) atomicOr(&a.sat[W.psi[lane]], 1u << q);
+                }
+            }
+            over = over || ran_out;
             __syncwarp();
         }
     }
@@ -873,10 +973,11 @@ k_final_items(SearchArgs a) {
         const int64_t it1 = min(a.n_items, it0 + kItemBatch);
         const unsigned long long before = matches;
         for (int64_t it = it0; it < it1 && !over; it++) {
-            const int4 item = a.items[it];
-            if (lane == 0) { W.psi[0] = item.x; W.psi[1] = item.y; W.psi[2] = item.z; }
+            const SearchItem item = a.items[it];
+            const int depth = item.hd >> 8;
+            if (lane < depth) W.psi[lane] = item.psi[lane];
             __syncwarp();
-            search_from<true>(a, a.plans[0], item.w >> 8, W, entries, matches, over);
+            search_from<true>(a, a.plans[0], depth, W, entries, matches, over);
             __syncwarp();
         }
         if (matches != before) {
@@ -1018,9 +1119,9 @@ struct Workspace {
     int64_t acc_cap = 0;
     int32_t *roots = nullptr;
     uint32_t *sat = nullptr;
-    int4 *items = nullptr;           // split search work
+    SearchItem *items = nullptr;     // split search work
     int64_t items_cap = 0;
-    int4 *items2 = nullptr;          // input of the second-level expansion
+    SearchItem *items2 = nullptr;    // input of a further expansion
     DevPlan *plans = nullptr;
     RoundStats *st = nullptr;        // device
     unsigned long long *next_root = nullptr;   // dynamic root counter of the searches
@@ -1118,7 +1219,7 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     if ((rc = dalloc(ctx, &w.acc, (size_t)w.acc_cap))) return rc;
     if ((rc = dalloc(ctx, &w.roots, (size_t)g->n))) return rc;
     if ((rc = dalloc(ctx, &w.sat, (size_t)g->n))) return rc;
-    w.items_cap = std::min<int64_t>(std::max<int64_t>(g->m, (int64_t)1 << 22), (int64_t)1 << 25);
+    w.items_cap = std::min<int64_t>(std::max<int64_t>(g->m, (int64_t)1 << 22), (int64_t)1 << 24);
     if ((rc = dalloc(ctx, &w.items, (size_t)w.items_cap))) return rc;
     if ((rc = dalloc(ctx, &w.items2, (size_t)kExpandBelow))) return rc;
     if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxT))) return rc;
@@ -1165,19 +1266,24 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
     return CCPM_OK;
 }
 
-// Split search work one level deeper when there is too little of it.
-int expand_more(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int64_t &launches) {
-    if (a.n_items <= 0 || a.n_items >= kExpandBelow) return CCPM_OK;
-    CU(ctx, cudaMemcpyAsync(w.items2, w.items, sizeof(int4) * (size_t)a.n_items, cudaMemcpyDeviceToDevice, ctx->stream));
-    CU(ctx, cudaMemsetAsync(&w.st->n_items, 0, sizeof(unsigned int), ctx->stream));
-    launches++;
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_items + 3) / 4, (int64_t)ctx->num_sms * 16));
-    k_expand2<<<grid, 128, 0, ctx->stream>>>(a, w.items2, a.n_items);
-    CU(ctx, cudaGetLastError());
-    unsigned int n2 = 0;
-    CU(ctx, cudaMemcpyAsync(&n2, &w.st->n_items, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(ctx, cudaStreamSynchronize(ctx->stream));
-    a.n_items = n2;
+// Split search work level by level while there is too little of it to fill
+// the GPU (and the items still leave positions to place).
+int expand_more(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int max_depth, int64_t &launches) {
+    for (int depth = 2; depth < max_depth && depth < kItemMaxDepth; depth++) {
+        if (a.n_items <= 0 || a.n_items >= kExpandBelow) return CCPM_OK;
+        CU(ctx, cudaMemcpyAsync(w.items2, w.items, sizeof(SearchItem) * (size_t)a.n_items, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+        CU(ctx, cudaMemsetAsync(&w.st->n_items, 0, sizeof(unsigned int), ctx->stream));
+        launches++;
+        int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_items + 3) / 4, (int64_t)ctx->num_sms * 16));
+        k_expand_next<<<grid, 128, 0, ctx->stream>>>(a, w.items2, a.n_items);
+        CU(ctx, cudaGetLastError());
+        unsigned int n2 = 0;
+        CU(ctx, cudaMemcpyAsync(&n2, &w.st->n_items, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        if ((int64_t)n2 > w.items_cap) return set_err(ctx, CCPM_EOVERFLOW, "search items overflow");
+        a.n_items = n2;
+    }
     return CCPM_OK;
 }
 
@@ -1204,6 +1310,7 @@ struct Pipeline {
     const Template *t;
     DevTmpl dt;
     int cur = 0;            // omega buffer holding round-k state
+    bool dense = true;      // next round is the first after init: all edge bits set
     int li = 0;             // frontier list parity
     int64_t n_small = 0, n_med = 0, n_chunk = 0;
     int64_t scanned = 0;
@@ -1243,9 +1350,18 @@ struct Pipeline {
         launches++;
         lcc_launches++;
         // one resident wave: grid-stride work is split evenly over warps that all run at once
-        if (maxc == 0) k_lcc_round<0><<<lcc_grid(ctx, k_lcc_round<0>, warps), 256, 0, ctx->stream>>>(a, dt);
-        else if (maxc <= 4) k_lcc_round<4><<<lcc_grid(ctx, k_lcc_round<4>, warps), 256, 0, ctx->stream>>>(a, dt);
-        else k_lcc_round<32><<<lcc_grid(ctx, k_lcc_round<32>, warps), 256, 0, ctx->stream>>>(a, dt);
+#define CCPM_LAUNCH_LCC(C, D) k_lcc_round<C, D><<<lcc_grid(ctx, k_lcc_round<C, D>, warps), 256, 0, ctx->stream>>>(a, dt)
+        if (dense) {
+            if (maxc == 0) CCPM_LAUNCH_LCC(0, true);
+            else if (maxc <= 4) CCPM_LAUNCH_LCC(4, true);
+            else CCPM_LAUNCH_LCC(32, true);
+        } else {
+            if (maxc == 0) CCPM_LAUNCH_LCC(0, false);
+            else if (maxc <= 4) CCPM_LAUNCH_LCC(4, false);
+            else CCPM_LAUNCH_LCC(32, false);
+        }
+#undef CCPM_LAUNCH_LCC
+        dense = false;      // only the first round after init sees every bit set
         CU(ctx, cudaGetLastError());
         return CCPM_OK;
     }
@@ -1611,7 +1727,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             CUF(cudaGetLastError());
             RCF(P.read_stats());
             a.n_items = w.st_h->n_items;
-            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, P.launches));
+            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, __builtin_popcount(c.vmask), P.launches));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             P.launches++;
             if (a.n_items <= w.items_cap) {
@@ -1687,7 +1803,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             CUF(cudaGetLastError());
             RCF(P.read_stats());
             a.n_items = w.st_h->n_items;
-            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, P.launches));
+            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, t.n0, P.launches));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             P.launches++;
             if (a.n_items <= w.items_cap) {
@@ -2001,9 +2117,9 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         a.st = st;
         a.hub_deg = hub;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
-        if (dt.n_cls == 0) k_lcc_round<0><<<g, 256, 0, s>>>(a, dt);
-        else if (dt.n_cls <= 4) k_lcc_round<4><<<g, 256, 0, s>>>(a, dt);
-        else k_lcc_round<32><<<g, 256, 0, s>>>(a, dt);
+        if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
+        else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);
+        else k_lcc_round<32, false><<<g, 256, 0, s>>>(a, dt);
         NA_CU(cudaGetLastError());
         NA_CU(read_stats());
         r++;
