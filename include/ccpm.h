@@ -64,11 +64,21 @@ extern "C" {
 /* constraint order (Section 3.2 "Constraint Ordering Heuristics") */
 #define CCPM_ORDER_FIXED    0  /* the paper's heuristic: paths and cycles first, shorter first */
 #define CCPM_ORDER_EXPLICIT 1  /* the order given by ccpm_tmpl_set_order                       */
+#define CCPM_ORDER_LEARNED  2  /* before each constraint, the remaining ones are scored by the
+                                  ordering network (options.mlp) and the best runs next; every
+                                  constraint still runs, so results equal the fixed order's     */
+
+/* ordering network: 16 features -> 64 -> 64 -> 1 (ReLU) */
+#define CCPM_MLP_IN      16
+#define CCPM_MLP_HIDDEN  64
+#define CCPM_MLP_PARAMS  (CCPM_MLP_IN * CCPM_MLP_HIDDEN + CCPM_MLP_HIDDEN + \
+                          CCPM_MLP_HIDDEN * CCPM_MLP_HIDDEN + CCPM_MLP_HIDDEN + CCPM_MLP_HIDDEN + 1)
 
 typedef struct ccpm_ctx    *ccpm_ctx_t;
 typedef struct ccpm_graph  *ccpm_graph_t;
 typedef struct ccpm_tmpl   *ccpm_tmpl_t;
 typedef struct ccpm_result *ccpm_result_t;
+typedef struct ccpm_mlp    *ccpm_mlp_t;
 
 typedef struct {
     int      kind;                 /* CCPM_KIND_*                                  */
@@ -87,8 +97,25 @@ typedef struct {
                                    /* 0 = library default                          */
     int      hub_degree;           /* rows longer than this are split across warps;*/
                                    /* 0 = library default                          */
-    int      reserved[8];
+    int      batch_workers;        /* ccpm_prune_batch: concurrent workers, 0 = the */
+                                   /* autotuned choice for this graph              */
+    int      reserved[7];
+    ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
+
+/* What happened to one non-local constraint during a prune (the training log
+ * of the ordering network).  features are the network's inputs at the moment
+ * the constraint was chosen; bits_* are sums of |omega(v)| over all vertices
+ * before the constraint and after its LCC re-run. */
+typedef struct {
+    int32_t  constraint;           /* index in the generated (fixed) order          */
+    int32_t  position;             /* 0-based position at which it ran              */
+    float    features[CCPM_MLP_IN];
+    int64_t  bits_before, bits_after;
+    int32_t  lcc_rounds;           /* LCC rounds of the re-run (0 if nothing changed)*/
+    int32_t  tokens;               /* (vertex, head) walks it issued                 */
+    double   ms_search, ms_lcc;    /* device time of its search and of the re-run   */
+} ccpm_constraint_log;
 
 typedef struct {
     int64_t  active_v;             /* vertices with omega != 0 at the end         */
@@ -176,6 +203,19 @@ int  ccpm_tmpl_set_order(ccpm_tmpl_t t, int n, const int32_t *order);
 int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
                 const ccpm_options *opt, ccpm_result_t *out);
 
+/* Prune T templates over the same resident graph (the exploratory-search
+ * workload of Section 7.2: many variants of one query).  Each template's
+ * results are exactly those ccpm_prune gives for it.  The templates run
+ * concurrently on worker streams of this context, each with its own scratch,
+ * so that small phases of different templates overlap on the GPU; the number
+ * of workers comes from options.batch_workers or, when 0, from an autotuner
+ * that times candidate worker counts on the first call for this graph and
+ * keeps the fastest.  outs[i] follows the same create-or-reuse rule as
+ * ccpm_prune.  Returns CCPM_OK, CCPM_EBUDGET if any template hit a budget
+ * (see each result's counts), or the first error. */
+int  ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *tmpls,
+                      const ccpm_options *opt, ccpm_result_t *outs);
+
 /* ----------------------------------------------------------------- result */
 
 /* Copy omega (n uint32) to dst (host memory, or device memory when
@@ -188,9 +228,37 @@ int  ccpm_result_counts(ccpm_result_t r, ccpm_counts *out);
  * constraint changed nothing has 0 rounds.  Writes min(cap, n_phases). */
 int  ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap);
 /* Device pointers owned by the result (valid until it is destroyed). */
+/* Log record of the i-th constraint in the order it ran (0 <= i < n_phases-1). */
+int  ccpm_result_constraint_log(ccpm_result_t r, int i, ccpm_constraint_log *out);
 const uint32_t *ccpm_result_omega_device(ccpm_result_t r);
 const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r);
 void ccpm_result_destroy(ccpm_result_t r);
+
+/* ------------------------------------------------------ ordering network */
+
+/* A 3-layer perceptron that scores non-local constraints for
+ * CCPM_ORDER_LEARNED (the paper orders constraints by a fixed heuristic,
+ * Section 3.2, and leaves learned orders to future work, Section 9).
+ * Parameters: FP32 master copy of CCPM_MLP_PARAMS floats laid out as
+ * W1[16][64], b1[64], W2[64][64], b2[64], w3[64], b3 (W[i][j]: input i to
+ * unit j).  Products run on BF16 tensor cores with FP32 accumulation:
+ * X, W1, W2 and the first hidden layer are rounded to BF16 before each product.
+ * All host arrays are row-major FP32; calls are synchronous on the stream of
+ * the context the network was created on. */
+int  ccpm_mlp_create(ccpm_ctx_t ctx, uint64_t seed, ccpm_mlp_t *out);
+void ccpm_mlp_destroy(ccpm_mlp_t m);
+int  ccpm_mlp_set_params(ccpm_mlp_t m, const float *params);
+int  ccpm_mlp_get_params(ccpm_mlp_t m, float *params);
+/* y[b] = network(x[b][0..15]) for b < B. */
+int  ccpm_mlp_forward(ccpm_mlp_t m, int B, const float *x, float *y);
+/* Gradient of 0.5 * mean_b (y[b] - t[b])^2 with respect to every parameter
+ * (same layout as the parameters) and the loss itself. */
+int  ccpm_mlp_gradient(ccpm_mlp_t m, int B, const float *x, const float *t, float *grad, float *loss);
+/* `steps` Adam steps (beta 0.9 / 0.999) on minibatches of `batch` rows drawn
+ * with replacement from the N rows of (x, t) by a seeded counter-based hash;
+ * *final_loss (nullable) gets the last minibatch's loss. */
+int  ccpm_mlp_train(ccpm_mlp_t m, int N, const float *x, const float *t, int steps, int batch, float lr,
+                    uint64_t seed, float *final_loss);
 
 /* ------------------------------------------------- allocation-free LCC */
 

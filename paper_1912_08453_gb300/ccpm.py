@@ -20,7 +20,9 @@ _LIB_PATH = os.path.join(_HERE, "libccpm.so")
 CCPM_OK, CCPM_EINVAL, CCPM_ENOMEM, CCPM_ECUDA = 0, 1, 2, 3
 CCPM_ETIMEOUT, CCPM_EOVERFLOW, CCPM_EBUDGET, CCPM_ESTATE = 4, 5, 6, 7
 CCPM_HOST_PTRS, CCPM_DEVICE_PTRS, CCPM_VALIDATE = 0, 1, 2
-CCPM_ORDER_FIXED, CCPM_ORDER_EXPLICIT = 0, 1
+CCPM_ORDER_FIXED, CCPM_ORDER_EXPLICIT, CCPM_ORDER_LEARNED = 0, 1, 2
+MLP_IN, MLP_HIDDEN = 16, 64
+MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 KIND_NAMES = {0: "PC", 1: "CC", 2: "TDS_CC", 3: "TDS_PC", 4: "TDS"}
 MAX_TMPL_EDGES = 496
 
@@ -34,7 +36,8 @@ class CcpmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("order_mode", ctypes.c_int), ("run_final", ctypes.c_int),
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
-                ("hub_degree", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("reserved", ctypes.c_int * 7),
+                ("mlp", ctypes.c_void_p)]
 
 
 class Counts(ctypes.Structure):
@@ -52,6 +55,18 @@ class Counts(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ConstraintLog(ctypes.Structure):
+    _fields_ = [("constraint", ctypes.c_int32), ("position", ctypes.c_int32),
+                ("features", ctypes.c_float * MLP_IN), ("bits_before", ctypes.c_int64),
+                ("bits_after", ctypes.c_int64), ("lcc_rounds", ctypes.c_int32), ("tokens", ctypes.c_int32),
+                ("ms_search", ctypes.c_double), ("ms_lcc", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["features"] = list(self.features)
+        return d
 
 
 class ConstraintInfo(ctypes.Structure):
@@ -79,6 +94,7 @@ def _load():
         "ccpm_constraints_describe": ([vp, i32, P(ConstraintInfo)], i32),
         "ccpm_tmpl_set_order": ([vp, i32, vp], i32),
         "ccpm_prune": ([vp, vp, vp, P(Options), P(vp)], i32),
+        "ccpm_prune_batch": ([vp, vp, i32, P(vp), P(Options), P(vp)], i32),
         "ccpm_result_omega": ([vp, vp, i64, i32], i32),
         "ccpm_result_edge_bitmap": ([vp, vp, i64, i32], i32),
         "ccpm_result_counts": ([vp, P(Counts)], i32),
@@ -86,6 +102,14 @@ def _load():
         "ccpm_result_omega_device": ([vp], vp),
         "ccpm_result_edge_bitmap_device": ([vp], vp),
         "ccpm_result_destroy": ([vp], None),
+        "ccpm_result_constraint_log": ([vp, i32, P(ConstraintLog)], i32),
+        "ccpm_mlp_create": ([vp, ctypes.c_uint64, P(vp)], i32),
+        "ccpm_mlp_destroy": ([vp], None),
+        "ccpm_mlp_set_params": ([vp, vp], i32),
+        "ccpm_mlp_get_params": ([vp, vp], i32),
+        "ccpm_mlp_forward": ([vp, i32, vp, vp], i32),
+        "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
+        "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
         "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
                                        P(ctypes.c_int32), P(ctypes.c_int64), ctypes.c_char_p, ctypes.c_size_t], i32),
     }
@@ -102,9 +126,11 @@ lib = _load()
 EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_options_default",
             "ccpm_graph_load_csr", "ccpm_graph_destroy", "ccpm_tmpl_load", "ccpm_tmpl_destroy",
             "ccpm_constraints_generate", "ccpm_constraints_describe", "ccpm_tmpl_set_order",
-            "ccpm_prune", "ccpm_result_omega", "ccpm_result_edge_bitmap", "ccpm_result_counts",
+            "ccpm_prune", "ccpm_prune_batch", "ccpm_result_omega", "ccpm_result_edge_bitmap", "ccpm_result_counts",
             "ccpm_result_phase_rounds", "ccpm_result_omega_device",
-            "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc"]
+            "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc",
+            "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
+            "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train"]
 
 
 def _ptr(a):
@@ -270,6 +296,21 @@ class Result:
         lib.ccpm_result_phase_rounds(self.h, _ptr(out)[0], int(c["n_phases"]))
         return [int(x) for x in out[: c["n_phases"]]]
 
+    def logs(self):
+        """Per-constraint log records, in the order the constraints ran."""
+        out = []
+        for i in range(max(self.counts()["n_phases"] - 1, 0)):
+            rec = ConstraintLog()
+            rc = lib.ccpm_result_constraint_log(self.h, i, ctypes.byref(rec))
+            if rc:
+                raise CcpmError(rc, "ccpm_result_constraint_log")
+            out.append(rec.as_dict())
+        return out
+
+    def order(self):
+        """Generated-order indices of the constraints, in the order they ran."""
+        return [r["constraint"] for r in self.logs()]
+
     def close(self):
         if self.h:
             lib.ccpm_result_destroy(self.h)
@@ -318,3 +359,79 @@ def lcc_fixpoint_noalloc(device, row_ptr, col, labels, tmpl_labels, tmpl_edges, 
     if rc:
         raise CcpmError(rc, f"ccpm_lcc_fixpoint_noalloc: {err.value.decode()}")
     return rounds.value, scanned.value
+
+
+def prune_batch(ctx: Context, graph: Graph, tmpls, opts: Options | None = None, results=None,
+                allow_budget: bool = False):
+    """ccpm_prune_batch over a list of Templates; reuses `results` when given."""
+    T = len(tmpls)
+    th = (ctypes.c_void_p * T)(*[t.h for t in tmpls])
+    rh = (ctypes.c_void_p * T)(*[(r.h.value if r is not None else None) for r in (results or [None] * T)])
+    rc = lib.ccpm_prune_batch(ctx.h, graph.h, T, th, ctypes.byref(opts) if opts is not None else None, rh)
+    if rc and not (rc == CCPM_EBUDGET and allow_budget):
+        ctx.check(rc, "ccpm_prune_batch")
+    if results is not None:
+        return results
+    return [Result(graph, ctypes.c_void_p(rh[i])) for i in range(T)]
+
+
+class Mlp:
+    """The constraint-ordering network (BF16 tensor-core kernels in the library)."""
+
+    def __init__(self, ctx: Context, seed: int = 1):
+        h = ctypes.c_void_p()
+        ctx.check(lib.ccpm_mlp_create(ctx.h, seed, ctypes.byref(h)), "ccpm_mlp_create")
+        self.h, self.ctx = h, ctx
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        rc = lib.ccpm_mlp_get_params(self.h, _ptr(out)[0])
+        if rc:
+            raise CcpmError(rc, "ccpm_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        assert p.shape == (MLP_PARAMS,)
+        rc = lib.ccpm_mlp_set_params(self.h, _ptr(p)[0])
+        if rc:
+            raise CcpmError(rc, "ccpm_mlp_set_params")
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, MLP_IN))
+        y = np.zeros(x.shape[0], dtype=np.float32)
+        rc = lib.ccpm_mlp_forward(self.h, x.shape[0], _ptr(x)[0], _ptr(y)[0])
+        if rc:
+            raise CcpmError(rc, "ccpm_mlp_forward")
+        return y
+
+    def gradient(self, x, t):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, MLP_IN))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32).reshape(-1))
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        rc = lib.ccpm_mlp_gradient(self.h, x.shape[0], _ptr(x)[0], _ptr(t)[0], _ptr(g)[0], ctypes.byref(loss))
+        if rc:
+            raise CcpmError(rc, "ccpm_mlp_gradient")
+        return g, loss.value
+
+    def train(self, x, t, steps: int, batch: int = 256, lr: float = 1e-3, seed: int = 1) -> float:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, MLP_IN))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32).reshape(-1))
+        loss = ctypes.c_float()
+        rc = lib.ccpm_mlp_train(self.h, x.shape[0], _ptr(x)[0], _ptr(t)[0], steps, batch, lr, seed,
+                                ctypes.byref(loss))
+        if rc:
+            raise CcpmError(rc, "ccpm_mlp_train")
+        return loss.value
+
+    def close(self):
+        if self.h:
+            lib.ccpm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

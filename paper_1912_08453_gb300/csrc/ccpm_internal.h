@@ -67,6 +67,11 @@ struct Template {
     std::string err;
 };
 
+// glue between translation units (ccpm_kernels.cu, ccpm_mlp.cu)
+int ctx_device(ccpm_ctx *ctx);
+void *ctx_stream_ptr(ccpm_ctx *ctx);
+int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stream);
+
 // host helpers (ccpm_host.cpp)
 int  template_build(Template &t, int n0, const uint8_t *labels, int m0, const int32_t *edges);
 int  constraints_generate(Template &t, std::string &err);

@@ -23,6 +23,13 @@
 
 #include <cub/device/device_segmented_sort.cuh>
 
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <chrono>
+#include <mutex>
+#include <thread>
+
 #include "ccpm_internal.h"
 
 namespace ccpm {
@@ -1072,6 +1079,28 @@ k_materialize(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restr
 
 __global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
 
+// Per template vertex q: number of vertices with q in omega(v); slot 32: the
+// total of |omega(v)|.  Inputs of the ordering features and the logs.
+__global__ void __launch_bounds__(256)
+k_omega_hist(int64_t n, const uint32_t *__restrict__ om, int n0, unsigned long long *hist) {
+    unsigned int cnt[kMaxT];
+#pragma unroll
+    for (int q = 0; q < kMaxT; q++) cnt[q] = 0u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t w = __ldg(om + v);
+#pragma unroll
+        for (int q = 0; q < kMaxT; q++) cnt[q] += (w >> q) & 1u;
+    }
+    unsigned long long total = 0;
+    for (int q = 0; q < n0; q++) {
+        unsigned int c = __reduce_add_sync(FULL_MASK, cnt[q]);
+        total += c;
+        if (lane_id() == 0 && c) atomicAdd(&hist[q], (unsigned long long)c);
+    }
+    if (lane_id() == 0 && total) atomicAdd(&hist[kMaxT], total);
+}
+
 // Population counts for the result summary.
 __global__ void __launch_bounds__(256)
 k_count(int64_t n, const uint32_t *__restrict__ om, int64_t words, const uint32_t *__restrict__ eb,
@@ -1098,14 +1127,6 @@ k_count(int64_t n, const uint32_t *__restrict__ om, int64_t words, const uint32_
 
 using namespace ccpm;
 
-struct ccpm_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int num_sms = 0;
-    std::string err;
-};
-
 struct Workspace {
     int64_t n = 0, m = 0, words = 0;
     int hub_deg = 0;
@@ -1128,8 +1149,20 @@ struct Workspace {
     RoundStats *st_h = nullptr;      // pinned host mirror
     unsigned long long *cnt = nullptr;
     unsigned long long *cnt_h = nullptr;
+    unsigned long long *hist = nullptr;      // 33 counters (k_omega_hist)
+    unsigned long long *hist_h = nullptr;
     DevPlan *plans_h = nullptr;      // pinned staging for plan uploads
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
+};
+
+struct ccpm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string err;
+    Workspace ws;                         // scratch of prunes issued on this context
+    std::vector<ccpm_ctx *> workers;      // contexts of concurrent batch workers
 };
 
 struct ccpm_graph {
@@ -1142,7 +1175,8 @@ struct ccpm_graph {
     int64_t label_freq[256] = {};
     int32_t *lcol = nullptr;      // rows grouped by neighbour label (built on first search)
     uint8_t *nlab = nullptr;
-    Workspace ws;
+    std::mutex lrow_mu;           // concurrent batch workers build the grouped rows once
+    int tuned_workers = 0;        // batch worker count chosen by the autotuner
 };
 
 struct ccpm_tmpl {
@@ -1156,6 +1190,7 @@ struct ccpm_result {
     uint32_t *eb = nullptr;
     ccpm_counts counts{};
     std::vector<int32_t> phase_rounds;
+    std::vector<ccpm_constraint_log> logs;
 };
 
 namespace {
@@ -1192,14 +1227,16 @@ void ws_free(Workspace &w) {
     cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
     if (w.st_h) cudaFreeHost(w.st_h);
     if (w.cnt_h) cudaFreeHost(w.cnt_h);
+    cudaFree(w.hist);
+    if (w.hist_h) cudaFreeHost(w.hist_h);
     if (w.plans_h) cudaFreeHost(w.plans_h);
     for (auto &e : w.ev) if (e) cudaEventDestroy(e);
     w = Workspace{};
 }
 
 int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
-    Workspace &w = g->ws;
-    if (w.om[0] && w.hub_deg == hub_deg) return CCPM_OK;
+    Workspace &w = ctx->ws;
+    if (w.om[0] && w.hub_deg == hub_deg && w.n == g->n && w.m == g->m) return CCPM_OK;
     ws_free(w);
     w.n = g->n;
     w.m = g->m;
@@ -1228,6 +1265,8 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     if ((rc = dalloc(ctx, &w.next_root, 1))) return rc;
     CU(ctx, cudaMallocHost((void **)&w.st_h, sizeof(RoundStats)));
     CU(ctx, cudaMallocHost((void **)&w.cnt_h, 2 * sizeof(unsigned long long)));
+    CU(ctx, cudaMalloc((void **)&w.hist, (kMaxT + 1) * sizeof(unsigned long long)));
+    CU(ctx, cudaMallocHost((void **)&w.hist_h, (kMaxT + 1) * sizeof(unsigned long long)));
     CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxT * sizeof(DevPlan)));
     CU(ctx, cudaMemsetAsync(w.acc, 0, sizeof(HubAcc) * (size_t)w.acc_cap, ctx->stream));
     for (auto &e : w.ev) CU(ctx, cudaEventCreate(&e));
@@ -1238,6 +1277,7 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
 // neighbours' labels keeps ids ascending inside each label group.  Built once
 // per graph, the first time a search needs it.
 int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
+    std::lock_guard<std::mutex> lock(g->lrow_mu);
     if (g->lcol || g->m == 0) return CCPM_OK;
     int rc;
     uint8_t *keys = nullptr;
@@ -1304,6 +1344,36 @@ int grid_for(ccpm_ctx *ctx, int64_t work_items, int per_block, int blocks_per_sm
     return (int)std::min(need, cap);
 }
 
+// Ordering features of one constraint in the current state (alive[q] =
+// vertices with q in omega, total = sum of |omega|), step = constraints run.
+void constraint_features(const Template &t, const HostConstraint &c, const unsigned long long *alive,
+                         unsigned long long total, int step, int n_constraints, float *f) {
+    for (int i = 0; i < CCPM_MLP_IN; i++) f[i] = 0.f;
+    f[c.kind] = 1.f;
+    const int nv = __builtin_popcount(c.vmask), ne = (int)c.edges.size(), nh = __builtin_popcount(c.hmask);
+    f[5] = nv / 8.f;
+    f[6] = ne / 8.f;
+    f[7] = nh / 8.f;
+    double sh = 0, sv = 0, mn = 1e300, mx = 0;
+    for (int q = 0; q < t.n0; q++) {
+        if ((c.hmask >> q) & 1u) sh += (double)alive[q];
+        if ((c.vmask >> q) & 1u) {
+            sv += (double)alive[q];
+            mn = std::min(mn, (double)alive[q]);
+            mx = std::max(mx, (double)alive[q]);
+        }
+    }
+    if (mn > 1e299) mn = 0;
+    f[8] = (float)(std::log2(1.0 + sh) / 32.0);
+    f[9] = (float)(std::log2(1.0 + mn) / 32.0);
+    f[10] = (float)(std::log2(1.0 + mx) / 32.0);
+    f[11] = (float)(std::log2(1.0 + sv) / 32.0);
+    f[12] = (float)nv / (float)t.n0;
+    f[13] = (float)(ne - nv + 1) / 4.f;
+    f[14] = n_constraints ? (float)step / (float)n_constraints : 0.f;
+    f[15] = (float)(std::log2(1.0 + (double)total) / 32.0);
+}
+
 struct Pipeline {
     ccpm_ctx *ctx;
     ccpm_graph *g;
@@ -1319,15 +1389,28 @@ struct Pipeline {
     double ms_lcc_kernel = 0.0;
     int maxc = 0;
 
+    // alive counts per template vertex (w.hist_h[0..31]) and total bits ([32])
+    int omega_hist() {
+        Workspace &w = ctx->ws;
+        CU(ctx, cudaMemsetAsync(w.hist, 0, (kMaxT + 1) * sizeof(unsigned long long), ctx->stream));
+        launches++;
+        k_omega_hist<<<grid_for(ctx, g->n, 256, 4), 256, 0, ctx->stream>>>(g->n, w.om[cur], t->n0, w.hist);
+        CU(ctx, cudaGetLastError());
+        CU(ctx, cudaMemcpyAsync(w.hist_h, w.hist, (kMaxT + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return CCPM_OK;
+    }
+
     int read_stats() {
-        Workspace &w = g->ws;
+        Workspace &w = ctx->ws;
         CU(ctx, cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, ctx->stream));
         CU(ctx, cudaStreamSynchronize(ctx->stream));
         return CCPM_OK;
     }
 
     int launch_round() {
-        Workspace &w = g->ws;
+        Workspace &w = ctx->ws;
         LccArgs a;
         a.rp = g->rp;
         a.col = g->col;
@@ -1368,7 +1451,7 @@ struct Pipeline {
 
     // LCC to fixpoint; returns rounds via *rounds.
     int lcc(int64_t *rounds) {
-        Workspace &w = g->ws;
+        Workspace &w = ctx->ws;
         int64_t r = 0;
         for (;;) {
             CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), ctx->stream));
@@ -1400,6 +1483,11 @@ struct Pipeline {
 
 }  // namespace
 
+namespace ccpm {
+int ctx_device(ccpm_ctx *ctx) { return ctx->device; }
+void *ctx_stream_ptr(ccpm_ctx *ctx) { return (void *)ctx->stream; }
+}  // namespace ccpm
+
 extern "C" {
 
 void ccpm_options_default(ccpm_options *o) {
@@ -1410,6 +1498,7 @@ void ccpm_options_default(ccpm_options *o) {
     o->max_embeddings = 1ull << 32;
     o->search_budget = 0;
     o->hub_degree = 0;
+    o->batch_workers = 0;
 }
 
 int ccpm_ctx_create(int device, void *stream, ccpm_ctx_t *out) {
@@ -1439,6 +1528,8 @@ int ccpm_ctx_create(int device, void *stream, ccpm_ctx_t *out) {
 void ccpm_ctx_destroy(ccpm_ctx_t c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    for (ccpm_ctx *wk : c->workers) ccpm_ctx_destroy(wk);
+    ws_free(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1518,7 +1609,6 @@ int ccpm_graph_load_csr(ccpm_ctx_t ctx, int64_t n, int64_t m, const int64_t *row
 void ccpm_graph_destroy(ccpm_graph_t g) {
     if (!g) return;
     cudaSetDevice(g->ctx->device);
-    ws_free(g->ws);
     if (!g->borrowed) { cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab); }
     cudaFree(g->lcol);
     cudaFree(g->nlab);
@@ -1589,7 +1679,7 @@ int ccpm_tmpl_set_order(ccpm_tmpl_t t, int n, const int32_t *order) {
 
 int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_options *opt_in, ccpm_result_t *out) {
     if (!ctx || !g || !tm || !out) return CCPM_EINVAL;
-    if (g->ctx != ctx) return set_err(ctx, CCPM_EINVAL, "graph belongs to another context");
+    if (g->ctx->device != ctx->device) return set_err(ctx, CCPM_EINVAL, "graph lives on another device");
     ccpm_options opt;
     if (opt_in) opt = *opt_in; else ccpm_options_default(&opt);
     CU(ctx, cudaSetDevice(ctx->device));
@@ -1603,7 +1693,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     const uint64_t budget = opt.search_budget ? opt.search_budget : kDefaultSearchBudget;
     int rc = ws_ensure(ctx, g, hub_deg);
     if (rc) return rc;
-    Workspace &w = g->ws;
+    Workspace &w = ctx->ws;
     ccpm_result *r = *out;
     if (r && r->g != g) return set_err(ctx, CCPM_EINVAL, "result was made for another graph");
     bool fresh = false;
@@ -1686,9 +1776,38 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     int64_t tokens = 0;
     bool over = false;
     int nl_run = 0;
-    std::vector<int> order = t.order;
-    for (size_t ci = 0; ci < order.size(); ci++) {
-        const HostConstraint &c = t.k0[(size_t)order[ci]];
+    std::vector<int> remaining = t.order;
+    const int n_constraints = (int)remaining.size();
+    const bool learned = opt.order_mode == CCPM_ORDER_LEARNED && opt.mlp;
+    if (opt.order_mode == CCPM_ORDER_LEARNED && !opt.mlp)
+        return fail(set_err(ctx, CCPM_EINVAL, "CCPM_ORDER_LEARNED needs options.mlp"));
+    r->logs.clear();
+    if (n_constraints > 0) RCF(P.omega_hist());
+    for (int step = 0; step < n_constraints; step++) {
+        // features of every remaining constraint in the current state
+        std::vector<float> feats(remaining.size() * CCPM_MLP_IN);
+        for (size_t i = 0; i < remaining.size(); i++)
+            constraint_features(t, t.k0[(size_t)remaining[i]], w.hist_h, w.hist_h[kMaxT], step, n_constraints,
+                                &feats[i * CCPM_MLP_IN]);
+        size_t pick = 0;
+        if (learned && remaining.size() > 1) {
+            std::vector<float> score(remaining.size());
+            P.launches++;
+            RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
+            for (size_t i = 1; i < remaining.size(); i++)
+                if (score[i] > score[pick]) pick = i;
+        }
+        const int chosen = remaining[pick];
+        ccpm_constraint_log lg;
+        std::memset(&lg, 0, sizeof(lg));
+        lg.constraint = chosen;
+        lg.position = step;
+        std::memcpy(lg.features, &feats[pick * CCPM_MLP_IN], sizeof(lg.features));
+        lg.bits_before = (int64_t)w.hist_h[kMaxT];
+        remaining.erase(remaining.begin() + (long)pick);
+        const HostConstraint &c = t.k0[(size_t)chosen];
+        CUF(cudaEventRecord(w.ev[6], s));
+        const int64_t tokens_before = tokens;
         uint32_t sadj[kMaxT] = {};
         for (auto &e : c.edges) { sadj[e.first] |= 1u << e.second; sadj[e.second] |= 1u << e.first; }
         for (int h = 0; h < kMaxT; h++)
@@ -1746,13 +1865,25 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             tokens += (int64_t)w.st_h->tokens;
         }
         bool changed = n_roots > 0 && w.st_h->changed;
+        CUF(cudaEventRecord(w.ev[7], s));
         int64_t rr = 0;
         if (changed) {
             // the previous fixpoint's frontier holds every live vertex
             RCF(P.lcc(&rr));
         }
+        CUF(cudaEventRecord(w.ev[8], s));
         r->phase_rounds.push_back((int32_t)rr);
         total_rounds += rr;
+        RCF(P.omega_hist());      // synchronises; state for the next decision
+        float ms_a = 0.f, ms_b = 0.f;
+        cudaEventElapsedTime(&ms_a, w.ev[6], w.ev[7]);
+        cudaEventElapsedTime(&ms_b, w.ev[7], w.ev[8]);
+        lg.ms_search = ms_a;
+        lg.ms_lcc = ms_b;
+        lg.lcc_rounds = (int32_t)rr;
+        lg.tokens = (int32_t)std::min<int64_t>(tokens - tokens_before, INT32_MAX);
+        lg.bits_after = (int64_t)w.hist_h[kMaxT];
+        r->logs.push_back(lg);
     }
     CUF(cudaEventRecord(w.ev[2], s));
 
@@ -1872,6 +2003,101 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
 #undef RCF
 }
 
+// Run templates [lo, hi) of a batch on `W` worker contexts, one host thread
+// each, taking templates from a shared counter.  Returns the first error.
+static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, int lo, int hi, const ccpm_tmpl_t *tmpls,
+                     const ccpm_options *opt, ccpm_result_t *outs, int W, int *budget_hit) {
+    while ((int)ctx->workers.size() < W) {
+        ccpm_ctx *wk = nullptr;
+        int rc = ccpm_ctx_create(ctx->device, nullptr, &wk);
+        if (rc) return set_err(ctx, rc, "batch: worker context");
+        ctx->workers.push_back(wk);
+    }
+    // workers start after everything already queued on the caller's stream
+    cudaEvent_t ready;
+    CU(ctx, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CU(ctx, cudaEventRecord(ready, ctx->stream));
+    for (int i = 0; i < W; i++) CU(ctx, cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
+    std::atomic<int> next(lo);
+    std::atomic<int> first_err(0);
+    std::atomic<int> budget(0);
+    std::mutex err_mu;
+    std::string err_msg;
+    std::vector<std::thread> pool;
+    for (int i = 0; i < W; i++) {
+        ccpm_ctx *wk = ctx->workers[(size_t)i];
+        pool.emplace_back([&, wk]() {
+            cudaSetDevice(wk->device);
+            for (int k = next.fetch_add(1); k < hi; k = next.fetch_add(1)) {
+                if (first_err.load()) break;
+                int rc = ccpm_prune(wk, g, tmpls[k], opt, &outs[k]);
+                if (rc == CCPM_EBUDGET) {
+                    budget.store(1);
+                } else if (rc) {
+                    int zero = 0;
+                    if (first_err.compare_exchange_strong(zero, rc)) {
+                        std::lock_guard<std::mutex> lk(err_mu);
+                        err_msg = wk->err;
+                    }
+                }
+            }
+        });
+    }
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(ready);
+    if (budget.load()) *budget_hit = 1;
+    if (first_err.load()) return set_err(ctx, first_err.load(), "batch: " + err_msg);
+    return CCPM_OK;
+}
+
+int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *tmpls, const ccpm_options *opt_in,
+                     ccpm_result_t *outs) {
+    if (!ctx || !g || T < 0 || (T > 0 && (!tmpls || !outs))) return CCPM_EINVAL;
+    for (int i = 0; i < T; i++)
+        if (!tmpls[i]) return set_err(ctx, CCPM_EINVAL, "batch: NULL template");
+    ccpm_options opt;
+    if (opt_in) opt = *opt_in; else ccpm_options_default(&opt);
+    CU(ctx, cudaSetDevice(ctx->device));
+    // constraint generation is host work: do it here, not inside the workers
+    for (int i = 0; i < T; i++) {
+        if (!tmpls[i]->t.generated) {
+            std::string err;
+            int rc = constraints_generate(tmpls[i]->t, err);
+            if (rc) return set_err(ctx, rc, err);
+        }
+    }
+    int rc = ensure_label_rows(ctx, g);
+    if (rc) return rc;
+    int budget_hit = 0;
+    int start = 0;
+    int W = opt.batch_workers > 0 ? opt.batch_workers : g->tuned_workers;
+    if (W <= 0) {
+        // autotune: time candidate worker counts on successive slices of this
+        // batch (every slice's results are final) and keep the fastest per
+        // template; the choice is cached on the graph
+        const int cand[] = {4, 8, 16};
+        const int slice = std::max(1, std::min(T / 4, 8));
+        double best = 1e300;
+        int best_w = 8;
+        for (int c = 0; c < 3 && start + slice <= T; c++) {
+            auto t0 = std::chrono::steady_clock::now();
+            rc = run_batch(ctx, g, start, start + slice, tmpls, &opt, outs, cand[c], &budget_hit);
+            if (rc) return rc;
+            double per = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / slice;
+            if (per < best) { best = per; best_w = cand[c]; }
+            start += slice;
+        }
+        g->tuned_workers = best_w;
+        W = best_w;
+    }
+    if (start < T) {
+        rc = run_batch(ctx, g, start, T, tmpls, &opt, outs, std::min(W, T - start), &budget_hit);
+        if (rc) return rc;
+    }
+    if (budget_hit) return set_err(ctx, CCPM_EBUDGET, "a search budget was exceeded in the batch");
+    return CCPM_OK;
+}
+
 int ccpm_result_omega(ccpm_result_t r, uint32_t *dst, int64_t n, int dst_on_device) {
     if (!r || !dst || n != r->g->n) return CCPM_EINVAL;
     ccpm_ctx *ctx = r->g->ctx;
@@ -1883,12 +2109,18 @@ int ccpm_result_omega(ccpm_result_t r, uint32_t *dst, int64_t n, int dst_on_devi
 }
 
 int ccpm_result_edge_bitmap(ccpm_result_t r, uint32_t *dst, int64_t words, int dst_on_device) {
-    if (!r || !dst || words != r->g->ws.words) return CCPM_EINVAL;
+    if (!r || !dst || words != (r->g->m + 31) / 32) return CCPM_EINVAL;
     ccpm_ctx *ctx = r->g->ctx;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaMemcpyAsync(dst, r->eb, sizeof(uint32_t) * (size_t)words,
                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return CCPM_OK;
+}
+
+int ccpm_result_constraint_log(ccpm_result_t r, int i, ccpm_constraint_log *out) {
+    if (!r || !out || i < 0 || i >= (int)r->logs.size()) return CCPM_EINVAL;
+    *out = r->logs[(size_t)i];
     return CCPM_OK;
 }
 

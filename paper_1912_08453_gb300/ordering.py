@@ -1,0 +1,52 @@
+"""Learned ordering of non-local constraints: data, training and evaluation.
+
+The plain pipeline (fixed order, Section 3.2) logs, for every constraint it
+checks, the ordering features in the state where it was chosen, the omega bits
+it removed (with its LCC re-run) and its device time.  The network learns
+    target = log2(1 + bits removed) - log2(1 + microseconds spent),
+a benefit-per-cost score; with CCPM_ORDER_LEARNED the pipeline runs the
+best-scored remaining constraint next.  Every constraint is still checked, so
+omega, the edge bitmap and the match count equal the fixed order's; only the
+order, and with it the LCC round counts and the time, change.
+
+Training and inference run in the library's BF16 tensor-core kernels; this
+module only assembles arrays.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ccpm
+
+
+def target(rec) -> float:
+    removed = max(rec["bits_before"] - rec["bits_after"], 0)
+    cost_us = 1000.0 * (rec["ms_search"] + rec["ms_lcc"])
+    return float(np.log2(1.0 + removed) - np.log2(1.0 + cost_us))
+
+
+def collect_logs(ctx, graph, templates, repeats: int = 1):
+    """Run the fixed-order pipeline on every template; return (X, y)."""
+    X, y = [], []
+    result = None
+    for t in templates:
+        h = t if isinstance(t, ccpm.Template) else ccpm.Template(ctx, t.labels, t.edges)
+        for _ in range(repeats):
+            result = ccpm.prune(ctx, graph, h, ccpm.options(), result=None, allow_budget=True)
+            for rec in result.logs():
+                X.append(rec["features"])
+                y.append(target(rec))
+            result.close()
+    return np.asarray(X, dtype=np.float32).reshape(-1, ccpm.MLP_IN), np.asarray(y, dtype=np.float32)
+
+
+def train(ctx, X, y, steps: int = 2000, batch: int = 256, lr: float = 2e-3, seed: int = 1):
+    net = ccpm.Mlp(ctx, seed=seed)
+    net.train(X, y, steps=steps, batch=batch, lr=lr, seed=seed)
+    return net
+
+
+def learned_options(net, **kw):
+    o = ccpm.options(order_mode=ccpm.CCPM_ORDER_LEARNED, **kw)
+    o.mlp = net.h.value
+    return o

@@ -1,0 +1,61 @@
+"""Learned constraint ordering: identical results, oracle-exact round counts
+for the order it chose, and the time it saves over the fixed order."""
+import numpy as np
+import pytest
+
+from paper_1912_08453_gb300 import workloads as wl
+from oracle import pipeline
+from oracle import constraints as cgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1912_08453_gb300 import ccpm
+    return ccpm.Context(0)
+
+
+def random_templates(g, count, seed0):
+    pool = [L for L in wl.labels_by_frequency(g) if L > 0][:7]
+    out = []
+    for s in range(seed0, seed0 + 40 * count):
+        rng = np.random.default_rng(s)
+        t = wl.random_template(s, int(rng.integers(4, 8)), int(rng.integers(1, 4)), pool)
+        if len(cgen.generate(t.labels, t.edges)) >= 2:
+            out.append(t)
+        if len(out) == count:
+            break
+    return out
+
+
+def test_learned_order_is_exact_and_reports_gain(ctx, capsys):
+    from paper_1912_08453_gb300 import ccpm, ordering
+    g = wl.rmat_graph(16, seed=4)
+    graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
+    X, y = ordering.collect_logs(ctx, graph, random_templates(g, 40, 100))
+    assert X.shape[0] >= 80
+    net = ordering.train(ctx, X, y, steps=800)
+    evalset = random_templates(g, 12, 5000)
+    t_fixed = t_learned = 0.0
+    for i, t in enumerate(evalset):
+        h = ccpm.Template(ctx, t.labels, t.edges)
+        fixed = ccpm.prune(ctx, graph, h, ccpm.options(), allow_budget=True)
+        learned = ccpm.prune(ctx, graph, h, ordering.learned_options(net), allow_budget=True)
+        np.testing.assert_array_equal(fixed.omega(), learned.omega())
+        np.testing.assert_array_equal(fixed.edge_bitmap(), learned.edge_bitmap())
+        cf, cl = fixed.counts(), learned.counts()
+        assert cf["match_embeddings"] == cl["match_embeddings"]
+        assert sorted(learned.order()) == list(range(len(learned.order())))
+        t_fixed += cf["ms_total"]
+        t_learned += cl["ms_total"]
+        if i < 4:
+            # the oracle, given the same order, reproduces every phase's rounds
+            K = cgen.generate(t.labels, t.edges)
+            ref = pipeline.run(g.row_ptr, g.col, g.labels, t.labels, t.edges,
+                               constraints=[K[j] for j in learned.order()])
+            assert learned.phase_rounds() == ref.phase_rounds
+            np.testing.assert_array_equal(learned.omega(), ref.omega)
+    with capsys.disabled():
+        print(f"\nlearned order: {t_learned:.2f} ms vs fixed {t_fixed:.2f} ms "
+              f"({t_fixed / max(t_learned, 1e-9):.2f}x) over {len(evalset)} templates")

@@ -194,3 +194,31 @@ def test_full_size_rmat22_workload(ctx):
     for name, (tl, te) in cfg["templates"].items():
         gpu, ref = assert_parity(ctx, g, tl, te)
         assert ref.match_embeddings > 0, name
+
+
+def test_batch_equals_one_at_a_time(ctx):
+    # the batched entry point gives each template exactly its own prune
+    from paper_1912_08453_gb300 import ccpm
+    g = wl.rmat_graph(14, seed=12)
+    pool = [L for L in wl.labels_by_frequency(g) if L > 0][:6]
+    base = wl.Template([5, 4, 8, 7, 4, 5], [(0, 1), (1, 2), (1, 3), (3, 4), (3, 5), (2, 3)])
+    tmpls = [base] + wl.edit_variants(base, 11, seed=3, label_pool=pool, n_min=4, n_max=8)
+    graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
+    hs = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls]
+    for workers in (0, 3):
+        res = ccpm.prune_batch(ctx, graph, hs, ccpm.options(batch_workers=workers))
+        for t, h, r in zip(tmpls, hs, res):
+            one = ccpm.prune(ctx, graph, h)
+            np.testing.assert_array_equal(r.omega(), one.omega())
+            np.testing.assert_array_equal(r.edge_bitmap(), one.edge_bitmap())
+            assert r.phase_rounds() == one.phase_rounds()
+            assert r.counts()["match_embeddings"] == one.counts()["match_embeddings"]
+            one.close()
+        for r in res:
+            r.close()
+    # and every result also equals the oracle
+    for t, h in zip(tmpls[:4], hs[:4]):
+        r = ccpm.prune_batch(ctx, graph, [h])[0]
+        ref = pipeline.run(g.row_ptr, g.col, g.labels, t.labels, t.edges)
+        np.testing.assert_array_equal(r.omega(), ref.omega)
+        np.testing.assert_array_equal(r.edge_bitmap(), ref.ebits)
