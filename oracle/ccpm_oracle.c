@@ -213,6 +213,26 @@ static void make_order(search_t *s, uint32_t svert, int root)
     s->k = tail;
 }
 
+/* Order for a search rooted at the template edge (a, b): a, then b, then the
+ * rest of the template breadth first (neighbours in increasing id). */
+static void make_order_edge(search_t *s, uint32_t svert, int a, int b)
+{
+    int head = 0, tail = 0;
+    uint32_t seen = (1u << a) | (1u << b);
+    s->order[tail] = a; s->parent[tail] = -1; tail++;
+    s->order[tail] = b; s->parent[tail] = a; tail++;
+    while (head < tail) {
+        int x = s->order[head++];
+        for (int y = 0; y < 32; y++) {
+            if (!((svert >> y) & 1u) || ((seen >> y) & 1u)) continue;
+            if (!((s->sadj[x] >> y) & 1u)) continue;
+            seen |= 1u << y;
+            s->order[tail] = y; s->parent[tail] = x; tail++;
+        }
+    }
+    s->k = tail;
+}
+
 static int extend(search_t *s, int i)
 {
     if (i == s->k) {
@@ -315,8 +335,10 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
 /* active edge for every template edge.  Outputs: om_out[v] = {q : some match */
 /* has phi(q) = v}, A_out[e] = 1 iff e is the image of a template edge in    */
 /* some match (both directions), *count = number of matches phi.             */
-/* Returns OR_OK, or OR_EBUDGET once the count exceeds `cap` (outputs then   */
-/* incomplete).                                                              */
+/* Returns OR_OK, or OR_EBUDGET once the count exceeds `cap`: the count is   */
+/* then invalid, and om_out / A_out are finished by existence searches, one   */
+/* per (vertex, template vertex) and one per (entry, template edge), so they  */
+/* are exact all the same.                                                    */
 /* ------------------------------------------------------------------------ */
 int oracle_final(int64_t n, const int64_t *rp, const int32_t *col,
                  int n0, const uint32_t *tadj, int m0, const int32_t *tedges,
@@ -341,7 +363,42 @@ int oracle_final(int64_t n, const int64_t *rp, const int32_t *col,
         s.psi[0] = v;
         extend(&s, 1);
     }
-    *count = s.count;
+    if (!s.over_budget) {
+        *count = s.count;
+        *n_scanned += s.scanned;
+        return OR_OK;
+    }
+    memset(om_out, 0, sizeof(uint32_t) * (size_t)n);
+    memset(A_out, 0, (size_t)m);
+    s.enumerate = 0;
+    for (int q = 0; q < n0; q++) {
+        make_order(&s, all, q);
+        for (int64_t v = 0; v < n; v++) {
+            if (!((omega[v] >> q) & 1u)) continue;
+            for (int j = 0; j < 32; j++) s.psi[j] = -1;
+            s.psi[q] = v;
+            if (extend(&s, 1)) om_out[v] |= 1u << q;
+        }
+    }
+    for (int t = 0; t < m0; t++) {
+        int a = tedges[2 * t], b = tedges[2 * t + 1];
+        make_order_edge(&s, all, a, b);
+        for (int64_t x = 0; x < n; x++) {
+            if (!((omega[x] >> a) & 1u)) continue;
+            for (int64_t e = rp[x]; e < rp[x + 1]; e++) {
+                int64_t y = col[e];
+                if (!A[e] || !((omega[y] >> b) & 1u) || A_out[e]) continue;
+                for (int j = 0; j < 32; j++) s.psi[j] = -1;
+                s.psi[a] = x;
+                s.psi[b] = y;
+                if (extend(&s, 2)) {
+                    A_out[e] = 1;
+                    A_out[entry_of(rp, col, y, x)] = 1;
+                }
+            }
+        }
+    }
+    *count = 0;
     *n_scanned += s.scanned;
-    return s.over_budget ? OR_EBUDGET : OR_OK;
+    return OR_EBUDGET;
 }

@@ -105,8 +105,7 @@ def run(row_ptr, col, labels, tlabels, tedges, constraints=None,
     st, om_f, A_f, count, ns = final(g, tlabels, tedges, omega, A, max_embeddings, with_scanned=True)
     search_scanned += ns
     valid = st == 0
-    if valid:
-        omega, A = om_f, A_f
+    omega, A = om_f, A_f          # exact even when the count ran past its cap
     res = OracleResult(
         omega=omega, A=A, ebits=pack_bits(A), phase_rounds=phase,
         nlcc_changed=changed_list, match_embeddings=count if valid else 0,

@@ -358,7 +358,7 @@ void build_dev_tmpl(const Template &t, DevTmpl &d) {
 }
 
 void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int root,
-                const int64_t *label_freq, bool with_marks, DevPlan &p) {
+                const int64_t *label_freq, bool with_marks, DevPlan &p, int second) {
     std::memset(&p, 0, sizeof(p));
     int pos_of[kMaxT];
     for (int i = 0; i < kMaxT; i++) pos_of[i] = -1;
@@ -380,6 +380,7 @@ void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int roo
                 best = q; best_links = links; best_freq = f;
             }
         }
+        if (k == 1 && second >= 0) best = second;    // edge-rooted plan: position 1 is fixed
         if (best < 0) break;   // S disconnected: cannot happen for generated constraints
         int parent_pos = kMaxT;
         uint32_t back = 0, same = 0;

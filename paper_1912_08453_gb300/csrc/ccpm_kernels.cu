@@ -659,14 +659,10 @@ __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P
 // embeddings from this root (ENUM = true).  `over` is set when the window
 // budget ran out; for existence the root is then reported as satisfied, which
 // keeps the result a superset of the exact answer.
-template <bool ENUM>
-__device__ __forceinline__ void mark_match(const SearchArgs &a, const DevPlan &P, WarpSearch &W) {
+// Both directions of every template edge of the embedding in W.psi get their
+// bit in the output edge map (id-sorted entry indices).
+__device__ __forceinline__ void mark_edges(const SearchArgs &a, const DevPlan &P, const WarpSearch &W) {
     const int lane = (int)lane_id();
-    if (lane < P.k) {
-        int32_t x = W.psi[lane];
-        uint32_t bit = 1u << P.q[lane];
-        if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
-    }
     for (int t = lane; t < P.n_marks; t += 32) {
         int32_t x = W.psi[P.mark_a[t]], y = W.psi[P.mark_b[t]];
         int64_t e1 = find_entry(a.rp, a.col, x, y);
@@ -708,17 +704,32 @@ __device__ __forceinline__ bool test_candidate(const SearchArgs &a, const DevPla
     return true;
 }
 
+// omega*(psi(i)) gets q_i for every position of the match in W.psi.
+__device__ __forceinline__ void mark_vertices(const SearchArgs &a, const DevPlan &P, const WarpSearch &W) {
+    const int lane = (int)lane_id();
+    if (lane < P.k) {
+        const int32_t x = W.psi[lane];
+        const uint32_t bit = 1u << P.q[lane];
+        if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
+    }
+    __syncwarp();
+}
+
+// Search modes: does an embedding exist / count the embeddings / count them
+// and mark the vertices and edges of every one.
+constexpr int kExist = 0, kCount = 1, kMark = 2;
+
 // Depth-first search from positions 0..d0-1 already placed in W.psi.
-template <bool ENUM>
+template <int MODE>
 __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpSearch &W,
                             unsigned long long &entries, unsigned long long &matches, bool &over) {
     const int lane = (int)lane_id();
     const int k = P.k;
     uint64_t used = 0;
     if (d0 >= k) {                                  // the placed prefix is already a full map
-        if (!ENUM) return true;
+        if (MODE == kExist) return true;
         matches++;
-        mark_match<ENUM>(a, P, W);
+        if (MODE == kMark) { mark_vertices(a, P, W); mark_edges(a, P, W); }
         return false;
     }
     open_level(a, P, W, d0);
@@ -728,11 +739,18 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
         if (m == 0u) {
             const int64_t pos = W.pos[d], end = W.end[d];
             if (pos >= end) { d--; continue; }
-            if (++used > a.budget) { over = true; return !ENUM; }
+            if (++used > a.budget) { over = true; return MODE == kExist; }
             entries += (unsigned long long)min((int64_t)32, end - pos);
             int32_t u;
             const bool ok = test_candidate(a, P, W, d, pos + lane, end, u);
             const uint32_t vm = __ballot_sync(FULL_MASK, ok);
+            if (MODE == kCount && d == k - 1) {
+                // counting: every valid image of the last position completes a match
+                matches += (unsigned long long)__popc(vm);
+                if (lane == 0) { W.mask[d] = 0u; W.pos[d] = pos + 32; }
+                __syncwarp();
+                continue;
+            }
             if (lane == 0) { W.mask[d] = vm; W.wbase[d] = pos; W.pos[d] = pos + 32; }
             __syncwarp();
             continue;
@@ -741,11 +759,10 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
         if (lane == 0) { W.mask[d] = m & (m - 1u); W.psi[d] = __ldg(a.lcol + W.wbase[d] + b); }
         __syncwarp();
         if (d == k - 1) {
-            if (!ENUM) return true;
-            matches++;
-            // mark the match: omega*(psi(i)) gets q_i, both directions of
-            // every template edge get their bit (id-sorted entry indices)
-            mark_match<ENUM>(a, P, W);
+            if (MODE == kExist) return true;
+            matches++;                              // kMark (counting never stores last-level masks)
+            mark_vertices(a, P, W);
+            mark_edges(a, P, W);
             continue;
         }
         d++;
@@ -776,7 +793,7 @@ k_nlcc_search(SearchArgs a) {
             const int h = __ffs(hm) - 1;
             if (lane == 0) W.psi[0] = v;
             __syncwarp();
-            if (search_from<false>(a, a.plans[h], 1, W, entries, matches, over)) sat |= 1u << h;
+            if (search_from<kExist>(a, a.plans[h], 1, W, entries, matches, over)) sat |= 1u << h;
             __syncwarp();
         }
         if (lane == 0) a.sat[v] = sat;
@@ -788,6 +805,7 @@ k_nlcc_search(SearchArgs a) {
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(128)
 k_final_search(SearchArgs a) {
     __shared__ WarpSearch ws[4];
@@ -804,7 +822,7 @@ k_final_search(SearchArgs a) {
         unsigned long long before = matches;
         if (lane == 0) W.psi[0] = v;
         __syncwarp();
-        search_from<true>(a, a.plans[0], 1, W, entries, matches, over);
+        search_from<MODE>(a, a.plans[0], 1, W, entries, matches, over);
         __syncwarp();
         if (matches != before) {
             unsigned long long tot = 0;
@@ -921,6 +939,8 @@ __device__ __forceinline__ int64_t grab_items(const SearchArgs &a, int batch) {
 }
 
 constexpr int kItemBatch = 4;
+constexpr int kMaxPlans = 64;      // plan slots (heads, or oriented template edges)
+constexpr uint64_t kMarkCap = 1ull << 20;   // matches one marking enumeration handles
 // Below this many first-level items the searches place position 2 as well.
 constexpr int64_t kExpandBelow = 16384;
 
@@ -944,15 +964,18 @@ k_nlcc_items(SearchArgs a) {
             if (lane < depth) W.psi[lane] = item.psi[lane];
             __syncwarp();
             bool ran_out = false;
-            if (search_from<false>(a, a.plans[h], depth, W, entries, matches, ran_out)) {
+            if (search_from<kExist>(a, a.plans[h], depth, W, entries, matches, ran_out)) {
                 const DevPlan &P = a.plans[h];
                 if (ran_out) {
                     // budget exhausted: keep the head (a superset of the exact answer)
                     if (lane == 0) atomicOr(&a.sat[item.psi[0]], bit);
-                } else if (lane < P.k) {
+                } else {
                     // the embedding found satisfies every head it places, not only h
-                    const int q = P.q[lane];
-                    if ((a.heads >> q) & 1u) atomicOr(&a.sat[W.psi[lane]], 1u << q);
+                    if (lane < P.k) {
+                        const int q = P.q[lane];
+                        if ((a.heads >> q) & 1u) atomicOr(&a.sat[W.psi[lane]], 1u << q);
+                    }
+                    if (a.eb_out) mark_edges(a, P, W);
                 }
             }
             over = over || ran_out;
@@ -965,6 +988,7 @@ k_nlcc_items(SearchArgs a) {
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(128)
 k_final_items(SearchArgs a) {
     __shared__ WarpSearch ws[4];
@@ -984,7 +1008,7 @@ k_final_items(SearchArgs a) {
             const int depth = item.hd >> 8;
             if (lane < depth) W.psi[lane] = item.psi[lane];
             __syncwarp();
-            search_from<true>(a, a.plans[0], depth, W, entries, matches, over);
+            search_from<MODE>(a, a.plans[0], depth, W, entries, matches, over);
             __syncwarp();
         }
         if (matches != before) {
@@ -999,6 +1023,104 @@ k_final_items(SearchArgs a) {
         }
     }
     if (lane == 0 && entries) atomicAdd(&a.st->windows, entries);
+}
+
+// Edge pass of the final step: every entry (x, y), x < y, whose ends hold
+// omega* sets joined by some template edge and that no embedding found so far
+// has marked becomes one item per orientation (a, b) of a template edge with
+// a in omega*(x), b in omega*(y); plans[o] is rooted at that oriented edge.
+struct EdgeTab {
+    int n;                       // oriented template edges in this pass
+    int8_t a[32], b[32];
+};
+
+__global__ void __launch_bounds__(256)
+k_edge_items(SearchArgs a, EdgeTab tab) {
+    __shared__ SearchItem sbuf[8][32];
+    __shared__ int scnt[8];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    if (lane == 0) scnt[wib] = 0;
+    __syncthreads();
+    WarpBuf<SearchItem> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
+    b.cap = (unsigned long long)a.items_cap;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+        const int32_t x = a.roots[it];
+        const uint32_t wx = __ldg(a.om + x);
+        const int64_t beg = a.rp[x], end = a.rp[x + 1];
+        for (int64_t base = beg; base < end; base += 32) {
+            const int64_t e = base + lane;
+            int32_t y = -1;
+            uint32_t wy = 0u;
+            if (e < end) {
+                y = __ldg(a.col + e);
+                if (y > x && !((a.eb_out[e >> 5] >> (uint32_t)(e & 31)) & 1u)) wy = __ldg(a.om + y);
+            }
+            for (int o = 0; o < tab.n; o++) {
+                const bool ok = wy && ((wx >> tab.a[o]) & 1u) && ((wy >> tab.b[o]) & 1u);
+                SearchItem si;
+                si.psi[0] = x;
+                si.psi[1] = y;
+                si.psi[5] = (int32_t)(e >> 32);
+                si.psi[6] = (int32_t)(e & 0xFFFFFFFF);
+                si.hd = o | (2 << 8);
+                b.push(ok, si);
+            }
+        }
+    }
+    b.flush();
+}
+
+__global__ void __launch_bounds__(128)
+k_edge_search(SearchArgs a) {
+    __shared__ WarpSearch ws[4];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    WarpSearch &W = ws[wib];
+    unsigned long long entries = 0, matches = 0;
+    bool over = false;
+    for (int64_t it0 = grab_items(a, kItemBatch); it0 < a.n_items; it0 = grab_items(a, kItemBatch)) {
+        const int64_t it1 = min(a.n_items, it0 + kItemBatch);
+        for (int64_t it = it0; it < it1; it++) {
+            const SearchItem item = a.items[it];
+            const int o = item.hd & 0xff;
+            const int64_t e = ((int64_t)(uint32_t)item.psi[5] << 32) | (int64_t)(uint32_t)item.psi[6];
+            uint32_t done = 0;                          // marked by an embedding found meanwhile?
+            if (lane == 0) done = (*(volatile uint32_t *)&a.eb_out[e >> 5] >> (uint32_t)(e & 31)) & 1u;
+            if (__shfl_sync(FULL_MASK, done, 0)) continue;
+            if (lane < 2) W.psi[lane] = item.psi[lane];
+            __syncwarp();
+            const DevPlan &P = a.plans[o];
+            bool ran_out = false;
+            if (search_from<kExist>(a, P, 2, W, entries, matches, ran_out)) {
+                if (!ran_out) {
+                    mark_edges(a, P, W);
+                } else if (lane == 0) {
+                    // budget exhausted: keep the edge (a superset of the exact answer)
+                    const int64_t e2 = find_entry(a.rp, a.col, item.psi[1], item.psi[0]);
+                    atomicOr(&a.eb_out[e >> 5], 1u << (uint32_t)(e & 31));
+                    if (e2 >= 0) atomicOr(&a.eb_out[e2 >> 5], 1u << (uint32_t)(e2 & 31));
+                }
+            }
+            over = over || ran_out;
+        }
+    }
+    if (lane == 0) {
+        if (entries) atomicAdd(&a.st->windows, entries);
+        if (over) atomicOr(&a.st->overflow, 1u);
+    }
+}
+
+// omega* of the roots from their satisfied bits.
+__global__ void k_sat_to_omega(const int32_t *roots, int64_t n_roots, const uint32_t *sat, const uint32_t *om,
+                               uint32_t *om_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_roots; i += stride) {
+        const int32_t v = roots[i];
+        om_out[v] = sat[v] & om[v];
+    }
 }
 
 // Label of the neighbour at every CSR entry (sort keys for the grouped rows).
@@ -1259,7 +1381,7 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     w.items_cap = std::min<int64_t>(std::max<int64_t>(g->m, (int64_t)1 << 22), (int64_t)1 << 24);
     if ((rc = dalloc(ctx, &w.items, (size_t)w.items_cap))) return rc;
     if ((rc = dalloc(ctx, &w.items2, (size_t)kExpandBelow))) return rc;
-    if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxT))) return rc;
+    if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxPlans))) return rc;
     if ((rc = dalloc(ctx, &w.st, 1))) return rc;
     if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
     if ((rc = dalloc(ctx, &w.next_root, 1))) return rc;
@@ -1267,7 +1389,7 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     CU(ctx, cudaMallocHost((void **)&w.cnt_h, 2 * sizeof(unsigned long long)));
     CU(ctx, cudaMalloc((void **)&w.hist, (kMaxT + 1) * sizeof(unsigned long long)));
     CU(ctx, cudaMallocHost((void **)&w.hist_h, (kMaxT + 1) * sizeof(unsigned long long)));
-    CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxT * sizeof(DevPlan)));
+    CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxPlans * sizeof(DevPlan)));
     CU(ctx, cudaMemsetAsync(w.acc, 0, sizeof(HubAcc) * (size_t)w.acc_cap, ctx->stream));
     for (auto &e : w.ev) CU(ctx, cudaEventCreate(&e));
     return CCPM_OK;
@@ -1789,14 +1911,30 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         for (size_t i = 0; i < remaining.size(); i++)
             constraint_features(t, t.k0[(size_t)remaining[i]], w.hist_h, w.hist_h[kMaxT], step, n_constraints,
                                 &feats[i * CCPM_MLP_IN]);
+        // a constraint none of whose heads is matched by a live vertex issues no
+        // token and changes nothing: it is checked without launching anything
+        auto is_noop = [&](size_t i) {
+            const uint32_t hm = t.k0[(size_t)remaining[i]].hmask;
+            for (int q = 0; q < t.n0; q++)
+                if (((hm >> q) & 1u) && w.hist_h[q]) return false;
+            return true;
+        };
         size_t pick = 0;
         if (learned && remaining.size() > 1) {
-            std::vector<float> score(remaining.size());
-            P.launches++;
-            RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
-            for (size_t i = 1; i < remaining.size(); i++)
-                if (score[i] > score[pick]) pick = i;
+            size_t first_noop = remaining.size();
+            for (size_t i = 0; i < remaining.size() && first_noop == remaining.size(); i++)
+                if (is_noop(i)) first_noop = i;
+            if (first_noop < remaining.size()) {
+                pick = first_noop;
+            } else {
+                std::vector<float> score(remaining.size());
+                P.launches++;
+                RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
+                for (size_t i = 1; i < remaining.size(); i++)
+                    if (score[i] > score[pick]) pick = i;
+            }
         }
+        const bool noop = is_noop(pick);
         const int chosen = remaining[pick];
         ccpm_constraint_log lg;
         std::memset(&lg, 0, sizeof(lg));
@@ -1806,6 +1944,13 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         lg.bits_before = (int64_t)w.hist_h[kMaxT];
         remaining.erase(remaining.begin() + (long)pick);
         const HostConstraint &c = t.k0[(size_t)chosen];
+        nl_run++;
+        if (noop) {
+            lg.bits_after = lg.bits_before;
+            r->logs.push_back(lg);
+            r->phase_rounds.push_back(0);
+            continue;
+        }
         CUF(cudaEventRecord(w.ev[6], s));
         const int64_t tokens_before = tokens;
         uint32_t sadj[kMaxT] = {};
@@ -1819,7 +1964,6 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         CUF(cudaGetLastError());
         RCF(P.read_stats());
         const int64_t n_roots = w.st_h->n_roots;
-        nl_run++;
         if (n_roots > 0) {
             RCF(ensure_label_rows(ctx, g));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
@@ -1874,7 +2018,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         CUF(cudaEventRecord(w.ev[8], s));
         r->phase_rounds.push_back((int32_t)rr);
         total_rounds += rr;
-        RCF(P.omega_hist());      // synchronises; state for the next decision
+        if (changed) RCF(P.omega_hist());      // state for the next decision
+        else CUF(cudaStreamSynchronize(s));
         float ms_a = 0.f, ms_b = 0.f;
         cudaEventElapsedTime(&ms_a, w.ev[6], w.ev[7]);
         cudaEventElapsedTime(&ms_b, w.ev[7], w.ev[8]);
@@ -1888,67 +2033,183 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     CUF(cudaEventRecord(w.ev[2], s));
 
     // ---- final template-driven search and match count (Remark 1, Sec. 4.6)
+    // omega* and E* are existence questions answered exactly by searches over
+    // the whole template; the number of matches is counted separately.
     bool count_valid = false;
     uint64_t matches = 0;
     bool final_done = false;
     if (opt.run_final) {
-        int root = 0;
-        for (int q = 1; q < t.n0; q++) {
-            if (g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]]) root = q;
-        }
-        uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
-        build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0]);
-        CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan), cudaMemcpyHostToDevice, s));
-        CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+        const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
+        RCF(ensure_label_rows(ctx, g));
         CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
         CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
-        P.launches++;
-        k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], 1u << root, w.roots, w.st);
-        CUF(cudaGetLastError());
-        RCF(P.read_stats());
-        const int64_t n_roots = w.st_h->n_roots;
-        if (n_roots > 0) {
-            RCF(ensure_label_rows(ctx, g));
-            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
-            SearchArgs a{};
-            a.rp = g->rp;
-            a.col = g->col;
-            a.lcol = g->lcol;
-            a.nlab = g->nlab;
-            a.om = w.om[P.cur];
-            a.roots = w.roots;
-            a.n_roots = n_roots;
-            a.next_root = w.next_root;
-            a.plans = w.plans;
+        SearchArgs a{};
+        a.rp = g->rp;
+        a.col = g->col;
+        a.lcol = g->lcol;
+        a.nlab = g->nlab;
+        a.roots = w.roots;
+        a.next_root = w.next_root;
+        a.plans = w.plans;
+        a.sat = w.sat;
+        a.eb_out = r->eb;
+        a.st = w.st;
+        a.budget = budget;
+        a.items = w.items;
+        a.items_cap = w.items_cap;
+        auto run_items = [&](bool edge_pass) -> int {
+            CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+            P.launches++;
+            const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
+            if (edge_pass) k_edge_search<<<gi, 128, 0, s>>>(a);
+            else k_nlcc_items<<<gi, 128, 0, s>>>(a);
+            CU(ctx, cudaGetLastError());
+            return P.read_stats();
+        };
+        int root = 0;
+        for (int q = 1; q < t.n0; q++)
+            if (g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]]) root = q;
+        // one pass over every match from roots of `root`: count (mode kCount) or
+        // count and mark (kMark); returns overflow of the cap
+        auto count_pass = [&](int mode, const uint32_t *om_src, uint64_t cap, uint64_t &found, bool &capped) -> int {
+            build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0]);
+            CU(ctx, cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan), cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+            P.launches++;
+            k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, om_src, 1u << root, w.roots, w.st);
+            CU(ctx, cudaGetLastError());
+            int rc2 = P.read_stats();
+            if (rc2) return rc2;
+            const int64_t nr = w.st_h->n_roots;
+            found = 0;
+            capped = false;
+            if (nr == 0) return CCPM_OK;
+            a.om = om_src;
+            a.n_roots = nr;
             a.heads = 1u << root;
+            a.cap = cap;
+            a.enum_heads = 1;
             a.om_out = r->om;
             a.eb_out = r->eb;
-            a.st = w.st;
-            a.budget = budget;
-            a.cap = opt.max_embeddings;
-            a.items = w.items;
-            a.items_cap = w.items_cap;
-            a.enum_heads = 1;
             P.launches++;
-            k_expand<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a);
-            CUF(cudaGetLastError());
-            RCF(P.read_stats());
+            k_expand<<<grid_for(ctx, nr * 32, 256, 8), 256, 0, s>>>(a);
+            CU(ctx, cudaGetLastError());
+            if ((rc2 = P.read_stats())) return rc2;
             a.n_items = w.st_h->n_items;
-            if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, t.n0, P.launches));
-            CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+            if (a.n_items <= w.items_cap && (rc2 = expand_more(ctx, w, a, t.n0, P.launches))) return rc2;
+            CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             P.launches++;
-            if (a.n_items <= w.items_cap) {
-                k_final_items<<<grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16), 128, 0, s>>>(a);
+            const bool use_items = a.n_items <= w.items_cap;
+            const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
+            const int gr = grid_for(ctx, nr * 32, 128, 16);
+            if (mode == kMark) {
+                if (use_items) k_final_items<kMark><<<gi, 128, 0, s>>>(a);
+                else k_final_search<kMark><<<gr, 128, 0, s>>>(a);
             } else {
-                k_final_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+                if (use_items) k_final_items<kCount><<<gi, 128, 0, s>>>(a);
+                else k_final_search<kCount><<<gr, 128, 0, s>>>(a);
             }
+            CU(ctx, cudaGetLastError());
+            if ((rc2 = P.read_stats())) return rc2;
+            P.windows += (int64_t)w.st_h->windows;
+            found = w.st_h->matches;
+            capped = w.st_h->overflow != 0;
+            return CCPM_OK;
+        };
+        // few matches: one enumeration that marks every match gives omega*,
+        // E* and the count at once
+        bool capped = false;
+        RCF(count_pass(kMark, w.om[P.cur], std::min<uint64_t>(opt.max_embeddings, kMarkCap), matches, capped));
+        if (!capped) {
+            count_valid = true;
+            final_done = true;
+        } else {
+            CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
+            CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
+            a.om_out = nullptr;
+            a.eb_out = r->eb;
+        }
+        if (!final_done) {
+            // (A) every (v, q): some match has phi(q) = v?  Found embeddings also
+            // satisfy the other (vertex, template vertex) pairs they place and mark
+            // their edges.
+            for (int q = 0; q < t.n0; q++) build_plan(t, all, t.adj, q, g->label_freq, true, w.plans_h[q]);
+            CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * (size_t)t.n0, cudaMemcpyHostToDevice, s));
+            CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+            P.launches++;
+            k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], all, w.roots, w.st);
             CUF(cudaGetLastError());
             RCF(P.read_stats());
+            int64_t n_roots = w.st_h->n_roots;
+            if (n_roots > 0) {
+                a.om = w.om[P.cur];
+                a.n_roots = n_roots;
+                a.heads = all;
+                a.enum_heads = 0;
+                P.launches++;
+                k_expand<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a);
+                CUF(cudaGetLastError());
+                RCF(P.read_stats());
+                a.n_items = w.st_h->n_items;
+                if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, t.n0, P.launches));
+                if (a.n_items <= w.items_cap) {
+                    RCF(run_items(false));
+                } else {
+                    CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+                    P.launches++;
+                    k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+                    CUF(cudaGetLastError());
+                    RCF(P.read_stats());
+                }
+                if (w.st_h->overflow) over = true;
+                P.windows += (int64_t)w.st_h->windows;
+                P.launches++;
+                k_sat_to_omega<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, w.sat, w.om[P.cur], r->om);
+                CUF(cudaGetLastError());
+            }
+            // (B) every entry between omega* vertices that no embedding has marked
+            // yet: some match maps a template edge onto it?
+            std::vector<std::pair<int, int>> oriented;
+            for (auto &e : t.edges) { oriented.push_back(e); oriented.push_back({e.second, e.first}); }
+            if (n_roots > 0) {
+                CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+                P.launches++;
+                k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, r->om, all, w.roots, w.st);
+                CUF(cudaGetLastError());
+                RCF(P.read_stats());
+                n_roots = w.st_h->n_roots;
+            }
+            for (size_t o0 = 0; n_roots > 0 && o0 < oriented.size(); o0 += 32) {
+                EdgeTab tab;
+                std::memset(&tab, 0, sizeof(tab));
+                tab.n = (int)std::min<size_t>(32, oriented.size() - o0);
+                for (int o = 0; o < tab.n; o++) {
+                    tab.a[o] = (int8_t)oriented[o0 + (size_t)o].first;
+                    tab.b[o] = (int8_t)oriented[o0 + (size_t)o].second;
+                    build_plan(t, all, t.adj, tab.a[o], g->label_freq, true, w.plans_h[o], tab.b[o]);
+                }
+                CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * (size_t)tab.n, cudaMemcpyHostToDevice, s));
+                CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+                a.om = r->om;
+                a.n_roots = n_roots;
+                P.launches++;
+                k_edge_items<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a, tab);
+                CUF(cudaGetLastError());
+                RCF(P.read_stats());
+                a.n_items = w.st_h->n_items;
+                if (a.n_items > w.items_cap)
+                    return fail(set_err(ctx, CCPM_EOVERFLOW, "edge pass: too many candidate edges"));
+                if (a.n_items > 0) {
+                    RCF(run_items(true));
+                    if (w.st_h->overflow) over = true;
+                    P.windows += (int64_t)w.st_h->windows;
+                }
+            }
+            // (C) many matches: count them over the exact omega*, up to the cap
+            RCF(count_pass(kCount, r->om, opt.max_embeddings, matches, capped));
+            count_valid = !capped;
         }
-        P.windows += (int64_t)w.st_h->windows;
-        matches = w.st_h->matches;
-        count_valid = !w.st_h->overflow;
-        final_done = count_valid;
+        final_done = true;
     }
     if (!final_done) {
         // hand back the pruned state: exact edge map for live rows, dead rows zeroed

@@ -14,7 +14,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -284,6 +286,10 @@ struct ccpm_mlp {
     cudaStream_t stream = nullptr;
     float *prm = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *sse = nullptr;
     int adam_step = 0;
+    // scoring scratch kept between calls (the pipeline scores before every constraint)
+    float *sx = nullptr, *sy = nullptr;
+    int s_cap = 0;
+    std::mutex mu;               // batch workers may score concurrently
 };
 
 namespace {
@@ -320,16 +326,25 @@ int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stre
     cudaStream_t s = (cudaStream_t)stream;
     if (!m || B <= 0) return CCPM_EINVAL;
     if (configure_kernels()) return CCPM_ECUDA;
-    Scratch sc;
-    if (cudaMalloc(&sc.x, sizeof(float) * (size_t)B * IN) != cudaSuccess ||
-        cudaMalloc(&sc.y, sizeof(float) * (size_t)B) != cudaSuccess)
-        return CCPM_ENOMEM;
-    cudaError_t e = cudaMemcpyAsync(sc.x, host_x, sizeof(float) * (size_t)B * IN, cudaMemcpyHostToDevice, s);
+    std::lock_guard<std::mutex> lock(m->mu);
+    if (B > m->s_cap) {
+        cudaFree(m->sx);
+        cudaFree(m->sy);
+        m->sx = m->sy = nullptr;
+        const int cap = std::max(B, 256);
+        if (cudaMalloc(&m->sx, sizeof(float) * (size_t)cap * IN) != cudaSuccess ||
+            cudaMalloc(&m->sy, sizeof(float) * (size_t)cap) != cudaSuccess) {
+            m->s_cap = 0;
+            return CCPM_ENOMEM;
+        }
+        m->s_cap = cap;
+    }
+    cudaError_t e = cudaMemcpyAsync(m->sx, host_x, sizeof(float) * (size_t)B * IN, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        k_mlp_forward<<<tiles(B), THREADS, fwd_smem(), s>>>(m->prm, sc.x, B, sc.y);
+        k_mlp_forward<<<tiles(B), THREADS, fwd_smem(), s>>>(m->prm, m->sx, B, m->sy);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_y, sc.y, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_y, m->sy, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? CCPM_OK : CCPM_ECUDA;
 }
@@ -382,6 +397,7 @@ void ccpm_mlp_destroy(ccpm_mlp_t m) {
     if (!m) return;
     cudaSetDevice(m->device);
     cudaFree(m->prm); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->sse);
+    cudaFree(m->sx); cudaFree(m->sy);
     delete m;
 }
 

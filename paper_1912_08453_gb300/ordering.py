@@ -19,24 +19,29 @@ import numpy as np
 from . import ccpm
 
 
-def target(rec) -> float:
+def target(rec, benefit_weight: float = 1.0) -> float:
+    """log2(1 + bits removed) * benefit_weight - log2(1 + microseconds)."""
     removed = max(rec["bits_before"] - rec["bits_after"], 0)
     cost_us = 1000.0 * (rec["ms_search"] + rec["ms_lcc"])
-    return float(np.log2(1.0 + removed) - np.log2(1.0 + cost_us))
+    return float(benefit_weight * np.log2(1.0 + removed) - np.log2(1.0 + cost_us))
 
 
-def collect_logs(ctx, graph, templates, repeats: int = 1):
-    """Run the fixed-order pipeline on every template; return (X, y)."""
-    X, y = [], []
+def collect_logs(ctx, graph, templates, repeats: int = 1, benefit_weight: float = 1.0, raw: bool = False):
+    """Run the fixed-order pipeline on every template; return (X, y), or the
+    raw log records when raw=True."""
+    X, y, recs = [], [], []
     result = None
     for t in templates:
         h = t if isinstance(t, ccpm.Template) else ccpm.Template(ctx, t.labels, t.edges)
         for _ in range(repeats):
             result = ccpm.prune(ctx, graph, h, ccpm.options(), result=None, allow_budget=True)
             for rec in result.logs():
+                recs.append(rec)
                 X.append(rec["features"])
-                y.append(target(rec))
+                y.append(target(rec, benefit_weight))
             result.close()
+    if raw:
+        return recs
     return np.asarray(X, dtype=np.float32).reshape(-1, ccpm.MLP_IN), np.asarray(y, dtype=np.float32)
 
 
@@ -50,3 +55,9 @@ def learned_options(net, **kw):
     o = ccpm.options(order_mode=ccpm.CCPM_ORDER_LEARNED, **kw)
     o.mlp = net.h.value
     return o
+
+
+def targets_from(recs, benefit_weight: float = 1.0):
+    X = np.asarray([r["features"] for r in recs], dtype=np.float32).reshape(-1, ccpm.MLP_IN)
+    y = np.asarray([target(r, benefit_weight) for r in recs], dtype=np.float32)
+    return X, y

@@ -26,7 +26,7 @@ def gpu_run(ctx, g, tl, te, **opt):
     from paper_1912_08453_gb300 import ccpm
     graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
     t = ccpm.Template(ctx, tl, te)
-    r = ccpm.prune(ctx, graph, t, ccpm.options(**opt))
+    r = ccpm.prune(ctx, graph, t, ccpm.options(**opt), allow_budget=True)
     out = dict(omega=r.omega(), ebits=r.edge_bitmap(), counts=r.counts(), phases=r.phase_rounds())
     r.close()
     t.close()
@@ -222,3 +222,18 @@ def test_batch_equals_one_at_a_time(ctx):
         ref = pipeline.run(g.row_ptr, g.col, g.labels, t.labels, t.edges)
         np.testing.assert_array_equal(r.omega(), ref.omega)
         np.testing.assert_array_equal(r.edge_bitmap(), ref.ebits)
+
+
+def test_count_cap_keeps_exact_sets(ctx):
+    # past max_embeddings the count is reported invalid; omega* and E* stay exact
+    g = wl.rmat_graph(12, seed=7)
+    g.labels = (np.arange(g.n) % 2).astype(np.uint8)
+    tl, te = [0, 1, 0, 1], [(0, 1), (1, 2), (2, 3), (3, 0)]
+    ref_full = pipeline.run(g.row_ptr, g.col, g.labels, tl, te)
+    assert ref_full.match_embeddings > 10
+    gpu = gpu_run(ctx, g, tl, te, max_embeddings=10)
+    ref = pipeline.run(g.row_ptr, g.col, g.labels, tl, te, max_embeddings=10)
+    assert gpu["counts"]["count_valid"] == 0 and not ref.count_valid
+    np.testing.assert_array_equal(gpu["omega"], ref.omega)
+    np.testing.assert_array_equal(gpu["ebits"], ref.ebits)
+    np.testing.assert_array_equal(ref.omega, ref_full.omega)

@@ -306,11 +306,18 @@ def test_order_invariance(seed):
         assert r.match_embeddings == base.match_embeddings
 
 
-def test_budget_reports_invalid_count():
-    g = wl.rmat_graph(8, seed=3)
-    g.labels = np.zeros(g.n, dtype=np.uint8)
-    r = pipeline.run(g.row_ptr, g.col, g.labels, [0, 0, 0], [(0, 1), (1, 2)], max_embeddings=10)
-    assert not r.count_valid and r.match_embeddings == 0
+def test_budget_reports_invalid_count_but_exact_sets():
+    # past the cap the count is invalid; omega* and E* are still exact
+    for seed in range(4):
+        g = random_graph(800 + seed, 9, 0.5, 2)
+        for tl, te in [([0, 1, 0], [(0, 1), (1, 2)]), ([0, 1, 0, 1], [(0, 1), (1, 2), (2, 3), (3, 0)])]:
+            wt, At, cnt = truth(g.row_ptr, g.col, g.labels, tl, te)
+            if cnt < 3:
+                continue
+            r = pipeline.run(g.row_ptr, g.col, g.labels, tl, te, max_embeddings=1)
+            assert not r.count_valid and r.match_embeddings == 0
+            np.testing.assert_array_equal(r.omega, wt)
+            np.testing.assert_array_equal(r.A, At)
 
 
 @pytest.mark.parametrize("k", [2, 3])
