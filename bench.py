@@ -72,6 +72,9 @@ def parse_args():
     p.add_argument("--workload", default="rmat22-degree", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--count-cap", type=int, default=1 << 30,
+                   help="matches counted per template before the count is reported invalid "
+                        "(omega* and E* stay exact)")
     return p.parse_args()
 
 
@@ -206,6 +209,10 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def graph_workers(graph):
+    return None
+
+
 def batch_templates(cfg):
     from paper_1912_08453_gb300 import workloads as wl
     (name, (tl, te)), = cfg["templates"].items()
@@ -227,7 +234,7 @@ def run_batch_workload(args, cfg):
     graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
     tmpls = batch_templates(cfg)
     hs = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls]
-    cap = ccpm.options(max_embeddings=1 << 30)
+    cap = ccpm.options(max_embeddings=args.count_cap)
 
     def plain(results):
         for i, h in enumerate(hs):
@@ -252,14 +259,24 @@ def run_batch_workload(args, cfg):
         recs = [rec for r in res_plain for rec in r.logs()]
         X, y = ordering.targets_from(recs)
         net = ordering.train(ctx, X, y, steps=2000) if len(recs) >= 8 else None
-        learned = ordering.learned_options(net, max_embeddings=1 << 30) if net else cap
+        learned = ordering.learned_options(net, max_embeddings=args.count_cap) if net else cap
         res_batch = ccpm.prune_batch(ctx, graph, hs, learned, allow_budget=True)   # autotunes workers
-        t_plain, t_batch = [], []
+        res_bfix = ccpm.prune_batch(ctx, graph, hs, cap, allow_budget=True)
+        res_plearn = [None] * len(hs)
+        t_plain, t_batch, t_bfix, t_plearn = [], [], [], []
         for _ in range(args.steps):
             _, ms = timed(lambda: plain(res_plain))
             t_plain.append(ms)
             _, ms = timed(lambda: ccpm.prune_batch(ctx, graph, hs, learned, results=res_batch, allow_budget=True))
             t_batch.append(ms)
+            _, ms = timed(lambda: ccpm.prune_batch(ctx, graph, hs, cap, results=res_bfix, allow_budget=True))
+            t_bfix.append(ms)
+
+            def plain_learned():
+                for i, h in enumerate(hs):
+                    res_plearn[i] = ccpm.prune(ctx, graph, h, learned, result=res_plearn[i], allow_budget=True)
+            _, ms = timed(plain_learned)
+            t_plearn.append(ms)
     same = all(np.array_equal(a.omega(), b.omega()) and np.array_equal(a.edge_bitmap(), b.edge_bitmap())
                and a.counts()["match_embeddings"] == b.counts()["match_embeddings"]
                for a, b in zip(res_plain, res_batch))
@@ -273,6 +290,11 @@ def run_batch_workload(args, cfg):
                        "template_sizes": sorted({t.n0 for t in tmpls}),
                        "l2": "inputs larger than L2 (the 513 MB column array)"},
             "plain_ms": ms_plain, "batched_learned_ms": ms_batch, "speedup": ms_plain / ms_batch,
+            "batched_fixed_ms": statistics.median(t_bfix), "plain_learned_ms": statistics.median(t_plearn),
+            "plain_split_ms": {k: sum(r.counts()[k] for r in res_plain) for k in ("ms_lcc", "ms_nlcc", "ms_final")},
+            "count_cap": args.count_cap,
+            "counts_valid": int(sum(r.counts()["count_valid"] for r in res_plain)),
+            "workers": graph_workers(graph),
             "identical_outputs": bool(same),
             "matches_total": int(sum(r.counts()["match_embeddings"] for r in res_batch)),
             "training_records": len(recs)}

@@ -1927,11 +1927,14 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             if (first_noop < remaining.size()) {
                 pick = first_noop;
             } else {
+                // the network predicts -log2(1 + microseconds) of running each
+                // constraint now; a constraint k places later in the fixed order
+                // runs first only if it is predicted more than 2^k times cheaper
                 std::vector<float> score(remaining.size());
                 P.launches++;
                 RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
                 for (size_t i = 1; i < remaining.size(); i++)
-                    if (score[i] > score[pick]) pick = i;
+                    if (score[i] - (float)i > score[pick] - (float)pick) pick = i;
             }
         }
         const bool noop = is_noop(pick);
@@ -2116,12 +2119,14 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             capped = w.st_h->overflow != 0;
             return CCPM_OK;
         };
-        // few matches: one enumeration that marks every match gives omega*,
-        // E* and the count at once
+        // count the matches (every match lies inside the pruned state); with
+        // few of them one more enumeration that marks each gives omega* and E*
         bool capped = false;
-        RCF(count_pass(kMark, w.om[P.cur], std::min<uint64_t>(opt.max_embeddings, kMarkCap), matches, capped));
-        if (!capped) {
-            count_valid = true;
+        RCF(count_pass(kCount, w.om[P.cur], opt.max_embeddings, matches, capped));
+        count_valid = !capped;
+        if (!capped && matches <= kMarkCap) {
+            uint64_t again = 0;
+            RCF(count_pass(kMark, w.om[P.cur], opt.max_embeddings, again, capped));
             final_done = true;
         } else {
             CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
@@ -2205,9 +2210,6 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                     P.windows += (int64_t)w.st_h->windows;
                 }
             }
-            // (C) many matches: count them over the exact omega*, up to the cap
-            RCF(count_pass(kCount, r->om, opt.max_embeddings, matches, capped));
-            count_valid = !capped;
         }
         final_done = true;
     }

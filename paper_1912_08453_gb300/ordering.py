@@ -3,9 +3,12 @@
 The plain pipeline (fixed order, Section 3.2) logs, for every constraint it
 checks, the ordering features in the state where it was chosen, the omega bits
 it removed (with its LCC re-run) and its device time.  The network learns
-    target = log2(1 + bits removed) - log2(1 + microseconds spent),
-a benefit-per-cost score; with CCPM_ORDER_LEARNED the pipeline runs the
-best-scored remaining constraint next.  Every constraint is still checked, so
+    target = -log2(1 + microseconds spent)
+(optionally plus benefit_weight * log2(1 + bits removed)), i.e. how cheap the
+constraint is to check in that state.  With CCPM_ORDER_LEARNED the pipeline
+keeps the fixed order as a prior: the constraint at position k among the
+remaining ones runs first only if it is predicted more than 2^k times cheaper
+than the fixed order's next one.  Every constraint is still checked, so
 omega, the edge bitmap and the match count equal the fixed order's; only the
 order, and with it the LCC round counts and the time, change.
 
@@ -19,14 +22,14 @@ import numpy as np
 from . import ccpm
 
 
-def target(rec, benefit_weight: float = 1.0) -> float:
+def target(rec, benefit_weight: float = 0.0) -> float:
     """log2(1 + bits removed) * benefit_weight - log2(1 + microseconds)."""
     removed = max(rec["bits_before"] - rec["bits_after"], 0)
     cost_us = 1000.0 * (rec["ms_search"] + rec["ms_lcc"])
     return float(benefit_weight * np.log2(1.0 + removed) - np.log2(1.0 + cost_us))
 
 
-def collect_logs(ctx, graph, templates, repeats: int = 1, benefit_weight: float = 1.0, raw: bool = False):
+def collect_logs(ctx, graph, templates, repeats: int = 1, benefit_weight: float = 0.0, raw: bool = False):
     """Run the fixed-order pipeline on every template; return (X, y), or the
     raw log records when raw=True."""
     X, y, recs = [], [], []
@@ -57,7 +60,7 @@ def learned_options(net, **kw):
     return o
 
 
-def targets_from(recs, benefit_weight: float = 1.0):
+def targets_from(recs, benefit_weight: float = 0.0):
     X = np.asarray([r["features"] for r in recs], dtype=np.float32).reshape(-1, ccpm.MLP_IN)
     y = np.asarray([target(r, benefit_weight) for r in recs], dtype=np.float32)
     return X, y
