@@ -216,6 +216,8 @@ struct LccArgs {
     HubAcc *acc;
     RoundStats *st;
     int hub_deg;
+    int med_chunk;                // medium vertices a warp prefetches together (1..16)
+    int small_chunk;              // short-row vertices a warp prefetches together (8, 16 or 32)
 };
 
 template <int MAXC>
@@ -245,12 +247,14 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const uint32_t *__restrict__ om, uint32_t *ebits,
                                               const SmemTmpl &s, Partial<MAXC> &p,
                                               unsigned long long &scanned) {
-    constexpr int UNR = 8;   // windows in flight
+    constexpr int UNR = 8;   // windows per step
     const int lane = (int)lane_id();
-    for (int64_t base = beg; base < end; base += 32 * UNR) {
+    // the column indices of the next step are loaded while the neighbour
+    // omegas of the current step are gathered
+    bool act[UNR];
+    int32_t u[UNR];
+    auto load_step = [&](int64_t base) {
         uint32_t word[UNR];
-        int32_t u[UNR];
-        bool act[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             const int64_t e = base + j * 32 + lane;
@@ -263,9 +267,13 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
             act[j] = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
             u[j] = act[j] ? __ldg(col + e) : 0;
         }
+    };
+    if (beg < end) load_step(beg);
+    for (int64_t base = beg; base < end; base += 32 * UNR) {
         uint32_t wu[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+        if (base + 32 * UNR < end) load_step(base + 32 * UNR);
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             const uint32_t w = wu[j];
@@ -447,55 +455,82 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         bc.push(lane == 0, ci);
     }
 
-    // (2) medium rows: one warp per vertex
-    for (int64_t it = gwarp; it < a.n_med; it += nwarps) {
-        const int32_t v = a.med_in[it];
-        const uint32_t wv = __ldg(a.om_cur + v);
-        uint32_t keep = 0u;
-        if (wv) {
-            const int64_t beg = a.rp[v], end = a.rp[v + 1];
-            if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
-            Partial<MAXC> p;
-            scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
-            p.U = grp_or<32>(p.U);
-            p.nN = grp_sum<32>(p.nN);
-            p.achg = grp_or<32>(p.achg);
-#pragma unroll
-            for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
-            keep = decide<MAXC>(wv, p, s);
-            if (keep != wv || p.achg) changed = 1u;
-            if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
+    // (2) medium rows: one warp per vertex, taken 16 at a time: the list
+    // entries, omega and row offsets of the next 16 vertices are loaded by 16
+    // lanes at once, so each row walk starts from registers
+    const int MB = a.med_chunk;
+    const int64_t n_mchunks = (a.n_med + MB - 1) / MB;
+    for (int64_t ch = gwarp; ch < n_mchunks; ch += nwarps) {
+        const int64_t idx = ch * MB + lane;
+        int32_t vl = -1;
+        uint32_t wl = 0u;
+        int64_t bl = 0, el = 0;
+        if (lane < MB && idx < a.n_med) {
+            vl = a.med_in[idx];
+            wl = __ldg(a.om_cur + vl);
+            if (wl) { bl = a.rp[vl]; el = a.rp[vl + 1]; }
         }
-        if (lane == 0) a.om_next[v] = keep;
-        bm.push(lane == 0 && wv != 0u, v);
+        for (int j = 0; j < MB; j++) {
+            const int32_t v = __shfl_sync(FULL_MASK, vl, j);
+            if (v < 0) break;
+            const uint32_t wv = __shfl_sync(FULL_MASK, wl, j);
+            const int64_t beg = __shfl_sync(FULL_MASK, bl, j), end = __shfl_sync(FULL_MASK, el, j);
+            uint32_t keep = 0u;
+            if (wv) {
+                if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
+                Partial<MAXC> p;
+                scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
+                p.U = grp_or<32>(p.U);
+                p.nN = grp_sum<32>(p.nN);
+                p.achg = grp_or<32>(p.achg);
+#pragma unroll
+                for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
+                keep = decide<MAXC>(wv, p, s);
+                if (keep != wv || p.achg) changed = 1u;
+                if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
+            }
+            if (lane == 0) a.om_next[v] = keep;
+            bm.push(lane == 0 && wv != 0u, v);
+        }
     }
 
-    // (3) short rows: 4 lanes per vertex, 8 vertices per warp step
+    // (3) short rows: 4 lanes per vertex, 8 vertices per warp step; the list
+    // entries, omega and row offsets of 32 vertices are loaded at once
     const int g = lane >> 2, lg = lane & 3;
-    const int64_t n_steps = (a.n_small + 7) / 8;
-    for (int64_t it = gwarp; it < n_steps; it += nwarps) {
-        const int64_t idx = it * 8 + g;
-        const int32_t v = idx < a.n_small ? a.small_in[idx] : -1;
-        const uint32_t wv = v >= 0 ? __ldg(a.om_cur + v) : 0u;
-        int64_t beg = 0, end = 0;
-        if (wv) { beg = a.rp[v]; end = a.rp[v + 1]; }
-        if (lg == 0 && wv) { rows += (unsigned long long)(end - beg); alive++; }
-        Partial<MAXC> p;
-        uint32_t clr = scan_row_group<4, MAXC, DENSE>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits, s, p,
-                                               scanned);
-        clr = grp_or<4>(clr);
-        p.achg = clr ? 1u : 0u;
-        if (lg == 0 && wv) clear_rel(a.ebits, beg, clr);
-        p.U = grp_or<4>(p.U);
-        p.nN = grp_sum<4>(p.nN);
-        p.achg = grp_or<4>(p.achg);
+    const int SB = a.small_chunk;
+    const int64_t n_schunks = (a.n_small + SB - 1) / SB;
+    for (int64_t ch = gwarp; ch < n_schunks; ch += nwarps) {
+        const int64_t idx = ch * SB + lane;
+        int32_t vl = -1;
+        uint32_t wl = 0u;
+        int64_t bl = 0, el = 0;
+        if (lane < SB && idx < a.n_small) {
+            vl = a.small_in[idx];
+            wl = __ldg(a.om_cur + vl);
+            if (wl) { bl = a.rp[vl]; el = a.rp[vl + 1]; }
+        }
+        for (int step = 0; step < SB / 8; step++) {
+            const int src = step * 8 + g;
+            const int32_t v = __shfl_sync(FULL_MASK, vl, src);
+            const uint32_t wv = __shfl_sync(FULL_MASK, wl, src);
+            const int64_t beg = __shfl_sync(FULL_MASK, bl, src), end = __shfl_sync(FULL_MASK, el, src);
+            if (lg == 0 && wv) { rows += (unsigned long long)(end - beg); alive++; }
+            Partial<MAXC> p;
+            uint32_t clr = scan_row_group<4, MAXC, DENSE>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits,
+                                                          s, p, scanned);
+            clr = grp_or<4>(clr);
+            p.achg = clr ? 1u : 0u;
+            if (lg == 0 && wv) clear_rel(a.ebits, beg, clr);
+            p.U = grp_or<4>(p.U);
+            p.nN = grp_sum<4>(p.nN);
 #pragma unroll
-        for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<4>(p.cnt[c]);
-        uint32_t keep = wv ? decide<MAXC>(wv, p, s) : 0u;
-        if (wv && (keep != wv || p.achg)) changed = 1u;
-        if (wv && keep == 0u) clear_row<4>(a.ebits, beg, end, lg);
-        if (v >= 0 && lg == 0) a.om_next[v] = keep;
-        bs.push(lg == 0 && wv != 0u, v);
+            for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<4>(p.cnt[c]);
+            uint32_t keep = wv ? decide<MAXC>(wv, p, s) : 0u;
+            if (wv && (keep != wv || p.achg)) changed = 1u;
+            if (wv && keep == 0u) clear_row<4>(a.ebits, beg, end, lg);
+            if (v >= 0 && lg == 0) a.om_next[v] = keep;
+            bs.push(lg == 0 && wv != 0u, v);
+        }
     }
 
     bs.flush();
@@ -1551,7 +1586,12 @@ struct Pipeline {
         a.acc = w.acc;
         a.st = w.st;
         a.hub_deg = w.hub_deg;
-        int64_t warps = n_chunk + n_med + (n_small + 7) / 8;
+        // prefetch units: large enough to hide the per-vertex loads, small
+        // enough that every resident warp gets several of them
+        const int64_t resident = (int64_t)ctx->num_sms * 32;
+        a.med_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, n_med / (4 * resident)));
+        a.small_chunk = n_small >= 32 * 4 * resident ? 32 : (n_small >= 16 * 4 * resident ? 16 : 8);
+        int64_t warps = n_chunk + (n_med + a.med_chunk - 1) / a.med_chunk + (n_small + a.small_chunk - 1) / a.small_chunk;
         launches++;
         lcc_launches++;
         // one resident wave: grid-stride work is split evenly over warps that all run at once
@@ -2611,6 +2651,8 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         a.acc = acc;
         a.st = st;
         a.hub_deg = hub;
+        a.med_chunk = 1;
+        a.small_chunk = 8;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
         if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
         else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);
