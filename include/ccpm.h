@@ -96,7 +96,8 @@ typedef struct {
     uint64_t search_budget;        /* max 32-candidate windows one root may scan;  */
                                    /* 0 = library default                          */
     int      hub_degree;           /* rows longer than this are split across warps;*/
-                                   /* 0 = library default                          */
+                                   /* 0 = library default (1024); values above    */
+                                   /* 2^24 are treated as 2^24                     */
     int      batch_workers;        /* ccpm_prune_batch: concurrent workers, 0 = the */
                                    /* autotuned choice for this graph              */
     int      reserved[7];

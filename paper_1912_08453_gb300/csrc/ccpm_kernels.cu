@@ -136,17 +136,26 @@ __device__ __forceinline__ void clear_row(uint32_t *ebits, int64_t beg, int64_t 
     }
 }
 
+// OR / sum over aligned groups of G lanes (whole warp: one redux instruction)
 template <int G>
 __device__ __forceinline__ uint32_t grp_or(uint32_t x) {
+    if constexpr (G == 32) {
+        return __reduce_or_sync(FULL_MASK, x);
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(FULL_MASK, x, o);
-    return x;
+        for (int o = G / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(FULL_MASK, x, o);
+        return x;
+    }
 }
 template <int G>
 __device__ __forceinline__ uint32_t grp_sum(uint32_t x) {
+    if constexpr (G == 32) {
+        return __reduce_add_sync(FULL_MASK, x);
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
-    return x;
+        for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+        return x;
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -235,9 +244,12 @@ struct Partial {
 // some q in omega(v)), the union omega' of Alg. 4 and the per-class counts of
 // distinct compatible neighbours.
 //
-// Warp form: all 32 lanes walk the row together, window by window (32
-// consecutive entries per window), so failing entries of a window are
-// cleared with one ballot and at most two atomics.
+// Warp form: all 32 lanes walk the row together in windows aligned to the
+// 32-entry words of the edge bitmap, so lane i of a window always owns bit i
+// of one word: the bits of a window are one broadcast load and its failing
+// entries are cleared with one ballot and one atomic.  Entry offsets are kept
+// relative to the first window (32-bit), so the loads of a step use one base
+// pointer with constant offsets.
 // DENSE: every edge bit of the rows read is still set (the first round after
 // init), so the bits are not loaded; otherwise a column index is only loaded
 // for entries whose bit is set.
@@ -246,34 +258,41 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const int32_t *__restrict__ col,
                                               const uint32_t *__restrict__ om, uint32_t *ebits,
                                               const SmemTmpl &s, Partial<MAXC> &p,
-                                              unsigned long long &scanned) {
-    constexpr int UNR = 8;   // windows per step
+                                              uint32_t &scanned) {
+    constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
+    const int64_t w0 = beg >> 5;
+    const int nwin = (int)(((end + 31) >> 5) - w0);
+    const int lo = (int)(beg - (w0 << 5));          // entries before lo belong to the previous row
+    const int hi = (int)(end - (w0 << 5));          // entries from hi on belong to the next row
+    const int32_t *cb = col + (w0 << 5) + lane;
+    uint32_t *eb = ebits + w0;
     // the column indices of the next step are loaded while the neighbour
     // omegas of the current step are gathered
     bool act[UNR];
     int32_t u[UNR];
-    auto load_step = [&](int64_t base) {
+    auto load_step = [&](int k0) {
+        const int rel0 = k0 * 32 + lane;
+        const int32_t *c0 = cb + k0 * 32;
         uint32_t word[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            const int64_t e = base + j * 32 + lane;
-            word[j] = DENSE ? ~0u : 0u;
-            if (!DENSE && e < end) word[j] = ebits[e >> 5];
+            word[j] = ~0u;
+            if (!DENSE) word[j] = (k0 + j < nwin) ? eb[k0 + j] : 0u;
         }
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            const int64_t e = base + j * 32 + lane;
-            act[j] = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
-            u[j] = act[j] ? __ldg(col + e) : 0;
+            const int rel = rel0 + j * 32;
+            act[j] = rel >= lo && rel < hi && ((word[j] >> lane) & 1u);
+            u[j] = act[j] ? __ldg(c0 + j * 32) : 0;
         }
     };
-    if (beg < end) load_step(beg);
-    for (int64_t base = beg; base < end; base += 32 * UNR) {
+    load_step(0);
+    for (int k0 = 0; k0 < nwin; k0 += UNR) {
         uint32_t wu[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
-        if (base + 32 * UNR < end) load_step(base + 32 * UNR);
+        if (k0 + UNR < nwin) load_step(k0 + UNR);
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             const uint32_t w = wu[j];
@@ -293,12 +312,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
             const uint32_t clr = __ballot_sync(FULL_MASK, fail);
             if (clr) {
                 p.achg = 1u;
-                if (lane == 0) {
-                    const int64_t e0 = base + j * 32;
-                    const uint32_t sh = (uint32_t)(e0 & 31);
-                    atomicAnd(&ebits[e0 >> 5], ~(clr << sh));
-                    if (sh && (clr >> (32 - sh))) atomicAnd(&ebits[(e0 >> 5) + 1], ~(clr >> (32 - sh)));
-                }
+                if (lane == 0) atomicAnd(&eb[k0 + j], ~clr);
             }
         }
     }
@@ -311,7 +325,7 @@ __device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uin
                                                    const int32_t *__restrict__ col,
                                                    const uint32_t *__restrict__ om, const uint32_t *ebits,
                                                    const SmemTmpl &s, Partial<MAXC> &p,
-                                                   unsigned long long &scanned) {
+                                                   uint32_t &scanned) {
     constexpr int UNR = 32 / G;   // covers the whole row in one pass
     uint32_t word[UNR];
     int32_t u[UNR];
@@ -398,7 +412,8 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     WarpBuf<ChunkItem> bc{cbuf[wib], &scnt[2][wib], a.chunk_out, &a.st->n_chunk};
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long scanned = 0, rows = 0, alive = 0;
+    uint32_t scanned = 0;          // per lane: at most one entry per window
+    unsigned long long rows = 0, alive = 0;
     uint32_t changed = 0;
 
     // (1) pieces of long rows: one warp per piece, combined through HubAcc;
@@ -537,14 +552,15 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     bm.flush();
     bc.flush();
     // warp totals
+    unsigned long long scanned64 = scanned;
     for (int o = 16; o > 0; o >>= 1) {
-        scanned += __shfl_xor_sync(FULL_MASK, scanned, o);
+        scanned64 += __shfl_xor_sync(FULL_MASK, scanned64, o);
         rows += __shfl_xor_sync(FULL_MASK, rows, o);
         alive += __shfl_xor_sync(FULL_MASK, alive, o);
         changed |= __shfl_xor_sync(FULL_MASK, changed, o);
     }
     if (lane == 0) {
-        if (scanned) atomicAdd(&a.st->scanned, scanned);
+        if (scanned64) atomicAdd(&a.st->scanned, scanned64);
         if (rows) atomicAdd(&a.st->row_entries, rows);
         if (alive) atomicAdd(&a.st->alive, alive);
         if (changed) atomicOr(&a.st->changed, 1u);
@@ -1851,7 +1867,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         int rc = constraints_generate(t, err);
         if (rc) return set_err(ctx, rc, err);
     }
-    const int hub_deg = opt.hub_degree > 0 ? opt.hub_degree : kDefaultHubDeg;
+    const int hub_deg = opt.hub_degree > 0 ? std::min(opt.hub_degree, kMaxHubDeg) : kDefaultHubDeg;
     const uint64_t budget = opt.search_budget ? opt.search_budget : kDefaultSearchBudget;
     int rc = ws_ensure(ctx, g, hub_deg);
     if (rc) return rc;
