@@ -100,7 +100,11 @@ typedef struct {
                                    /* 2^24 are treated as 2^24                     */
     int      batch_workers;        /* ccpm_prune_batch: concurrent workers, 0 = the */
                                    /* autotuned choice for this graph              */
-    int      reserved[7];
+    int      resume;               /* ccpm_prune: 1 = start from the state held in */
+                                   /* *out (a result of this graph and template,  */
+                                   /* e.g. one read back by ccpm_state_import)     */
+                                   /* instead of from the initial state of Alg. 3  */
+    int      reserved[6];
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 
@@ -234,6 +238,33 @@ int  ccpm_result_constraint_log(ccpm_result_t r, int i, ccpm_constraint_log *out
 const uint32_t *ccpm_result_omega_device(ccpm_result_t r);
 const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r);
 void ccpm_result_destroy(ccpm_result_t r);
+
+/* ------------------------------------------------------ checkpoint/resume */
+
+/* A pruning state (omega, edge bitmap, counts, per-phase rounds) as one
+ * self-describing host byte blob: a 96-byte little-endian header (magic
+ * "CCPMSTAT", version, n, m_dir, bitmap words, fingerprints of the graph -- n,
+ * m_dir and its label histogram -- and of the template -- labels and sorted
+ * edges --, sizes and an FNV-1a 64 checksum of the payload), then the counts,
+ * the phase rounds (int32), omega (n uint32) and the bitmap (words uint32).
+ * Constraint logs are not part of it.
+ *
+ * ccpm_state_export: with buf == NULL sets *len to the size needed and
+ * returns CCPM_OK; otherwise writes the blob to buf (host memory of *len
+ * bytes) and sets *len to the bytes written, or returns CCPM_EINVAL with *len
+ * set to the size needed when *len is too small.
+ *
+ * ccpm_state_import: checks the blob against g and t (CCPM_EINVAL on a wrong
+ * magic, version, size, fingerprint or checksum) and returns a new result in
+ * *out holding that state, owned by the caller like any result.  Pruning
+ * removes only candidates that no match uses (Section 3), so any state this
+ * library produced for (g, t) contains every match; ccpm_prune with
+ * options.resume = 1 continues from it (LCC, the non-local constraints and
+ * the final search) and ends in the same omega*, E* and match count as a
+ * fresh run; round counts may differ. */
+int  ccpm_state_export(ccpm_result_t r, void *buf, size_t *len);
+int  ccpm_state_import(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t, const void *buf, size_t len,
+                       ccpm_result_t *out);
 
 /* ------------------------------------------------------ ordering network */
 

@@ -36,7 +36,8 @@ class CcpmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("order_mode", ctypes.c_int), ("run_final", ctypes.c_int),
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
-                ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("reserved", ctypes.c_int * 7),
+                ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6),
                 ("mlp", ctypes.c_void_p)]
 
 
@@ -110,6 +111,8 @@ def _load():
         "ccpm_mlp_forward": ([vp, i32, vp, vp], i32),
         "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
         "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
+        "ccpm_state_export": ([vp, vp, P(ctypes.c_size_t)], i32),
+        "ccpm_state_import": ([vp, vp, vp, vp, ctypes.c_size_t, P(vp)], i32),
         "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
                                        P(ctypes.c_int32), P(ctypes.c_int64), ctypes.c_char_p, ctypes.c_size_t], i32),
     }
@@ -130,7 +133,8 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_result_phase_rounds", "ccpm_result_omega_device",
             "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc",
             "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
-            "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train"]
+            "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train",
+            "ccpm_state_export", "ccpm_state_import"]
 
 
 def _ptr(a):
@@ -311,6 +315,14 @@ class Result:
         """Generated-order indices of the constraints, in the order they ran."""
         return [r["constraint"] for r in self.logs()]
 
+    def export_state(self) -> bytes:
+        """ccpm_state_export: the state as one self-describing byte blob."""
+        n = ctypes.c_size_t(0)
+        self.graph.ctx.check(lib.ccpm_state_export(self.h, None, ctypes.byref(n)), "ccpm_state_export")
+        buf = ctypes.create_string_buffer(n.value)
+        self.graph.ctx.check(lib.ccpm_state_export(self.h, buf, ctypes.byref(n)), "ccpm_state_export")
+        return buf.raw[: n.value]
+
     def close(self):
         if self.h:
             lib.ccpm_result_destroy(self.h)
@@ -335,6 +347,15 @@ def prune(ctx: Context, graph: Graph, tmpl: Template, opts: Options | None = Non
         ctx.check(rc, "ccpm_prune")
     if result is not None:
         return result
+    return Result(graph, h)
+
+
+def state_import(ctx: Context, graph: Graph, tmpl: Template, blob: bytes) -> Result:
+    """ccpm_state_import: a result holding a saved state; prune it further with
+    options(resume=1) and result=<this result>."""
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    ctx.check(lib.ccpm_state_import(ctx.h, graph.h, tmpl.h, buf, len(blob), ctypes.byref(h)), "ccpm_state_import")
     return Result(graph, h)
 
 

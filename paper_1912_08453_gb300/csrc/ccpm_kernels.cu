@@ -166,8 +166,8 @@ struct LabelMask { uint32_t m[256]; };
 
 __global__ void __launch_bounds__(256)
 k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ lab, LabelMask lm,
-       uint32_t *om0, uint32_t *om1, int32_t *small_out, int32_t *med_out, ChunkItem *chunk_out,
-       RoundStats *st, int hub_deg) {
+       const uint32_t *__restrict__ om_in, uint32_t *om0, uint32_t *om1, int32_t *small_out, int32_t *med_out,
+       ChunkItem *chunk_out, RoundStats *st, int hub_deg) {
     __shared__ uint32_t slm[256];
     __shared__ int32_t sbuf[2][8][32];
     __shared__ int scnt[2][8];
@@ -184,6 +184,7 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
         int64_t deg = 0;
         if (v < n) {
             w = slm[lab[v]];
+            if (om_in) w &= om_in[v];     // resumed state, kept inside the initial one
             om0[v] = w;
             om1[v] = w;
             if (w) deg = rp[v + 1] - rp[v];
@@ -1251,6 +1252,7 @@ k_materialize(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restr
 }
 
 __global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
+__global__ void k_and_word(uint32_t *p, uint32_t v) { *p &= v; }
 
 // Per template vertex q: number of vertices with q in omega(v); slot 32: the
 // total of |omega(v)|.  Inputs of the ordering features and the logs.
@@ -1359,6 +1361,7 @@ struct ccpm_tmpl {
 
 struct ccpm_result {
     ccpm_graph *g = nullptr;
+    uint64_t tmpl_fp = 0;           // fingerprint of the template it was made for
     uint32_t *om = nullptr;
     uint32_t *eb = nullptr;
     ccpm_counts counts{};
@@ -1371,6 +1374,30 @@ namespace {
 int set_err(ccpm_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
     return code;
+}
+
+// FNV-1a 64 over a byte range (fingerprints and the checksum of saved states)
+uint64_t fnv1a(const void *p, size_t len, uint64_t h = 0xcbf29ce484222325ull) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < len; i++) { h ^= b[i]; h *= 0x100000001b3ull; }
+    return h;
+}
+
+// the template as labels and sorted edge list: equal for the same template
+// however its edges were listed
+uint64_t tmpl_fingerprint(const Template &t) {
+    std::vector<std::pair<int, int>> e = t.edges;
+    std::sort(e.begin(), e.end());
+    uint64_t h = fnv1a(&t.n0, sizeof(t.n0));
+    h = fnv1a(t.labels, (size_t)t.n0, h);
+    for (auto &x : e) { int32_t ab[2] = {x.first, x.second}; h = fnv1a(ab, sizeof(ab), h); }
+    return h;
+}
+
+uint64_t graph_fingerprint(const ccpm_graph &g) {
+    uint64_t h = fnv1a(&g.n, sizeof(g.n));
+    h = fnv1a(&g.m, sizeof(g.m), h);
+    return fnv1a(g.label_freq, sizeof(g.label_freq), h);
 }
 
 #define CU(ctx, call)                                                                 \
@@ -1874,6 +1901,10 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     Workspace &w = ctx->ws;
     ccpm_result *r = *out;
     if (r && r->g != g) return set_err(ctx, CCPM_EINVAL, "result was made for another graph");
+    const uint64_t tfp = tmpl_fingerprint(t);
+    const bool resume = opt.resume != 0;
+    if (resume && (!r || r->tmpl_fp != tfp))
+        return set_err(ctx, CCPM_EINVAL, "options.resume needs *out to hold a state of this graph and template");
     bool fresh = false;
     if (!r) {
         r = new (std::nothrow) ccpm_result();
@@ -1892,6 +1923,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     };
     std::memset(&r->counts, 0, sizeof(r->counts));
     r->phase_rounds.clear();
+    r->tmpl_fp = tfp;
 
     Pipeline P;
     P.ctx = ctx;
@@ -1920,19 +1952,36 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     LabelMask lm;
     std::memset(&lm, 0, sizeof(lm));
     for (int q = 0; q < t.n0; q++) lm.m[t.labels[q]] |= 1u << q;
-    CUF(cudaMemsetAsync(w.ebits, 0xFF, sizeof(uint32_t) * (size_t)w.words, s));
+    if (resume) {
+        // a saved state: its edge bits, then (below) its omega inside the initial one
+        CUF(cudaMemcpyAsync(w.ebits, r->eb, sizeof(uint32_t) * (size_t)w.words, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CUF(cudaMemsetAsync(w.ebits, 0xFF, sizeof(uint32_t) * (size_t)w.words, s));
+    }
     // no entries past m_dir: padding bits of the last word and the guard word stay 0
     k_set_word<<<1, 1, 0, s>>>(w.ebits + w.words, 0u);
     P.launches += 1 + ((g->m & 31) != 0);
-    if (g->m & 31) k_set_word<<<1, 1, 0, s>>>(w.ebits + w.words - 1, (1u << (uint32_t)(g->m & 31)) - 1u);
+    if (g->m & 31) {
+        const uint32_t pad = (1u << (uint32_t)(g->m & 31)) - 1u;
+        if (resume) k_and_word<<<1, 1, 0, s>>>(w.ebits + w.words - 1, pad);
+        else k_set_word<<<1, 1, 0, s>>>(w.ebits + w.words - 1, pad);
+    }
     CUF(cudaGetLastError());
     CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
     {
         int grid = grid_for(ctx, g->n, 256, 8);
         P.launches++;
-        k_init<<<grid, 256, 0, s>>>(g->n, g->rp, g->lab, lm, w.om[0], w.om[1], w.small[0], w.med[0],
+        k_init<<<grid, 256, 0, s>>>(g->n, g->rp, g->lab, lm, resume ? r->om : nullptr, w.om[0], w.om[1],
+                                    w.small[0], w.med[0],
                                     w.chunk[0], w.st, hub_deg);
         CUF(cudaGetLastError());
+    }
+    if (resume) {
+        // entries with a dead end point carry no bit; the first round reads the bits
+        P.launches++;
+        k_materialize<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[0], g->rp, g->col, w.ebits);
+        CUF(cudaGetLastError());
+        P.dense = false;
     }
     RCF(P.read_stats());
     P.cur = 0;
@@ -2467,6 +2516,119 @@ void ccpm_result_destroy(ccpm_result_t r) {
     delete r;
 }
 
+// ---- checkpoint/resume: one host blob per state (layout in ccpm.h)
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int64_t n, m_dir, words;
+    uint64_t graph_fp, tmpl_fp;
+    uint32_t counts_bytes, n_phases;
+    uint64_t payload_bytes;
+    uint64_t payload_fnv;
+    uint64_t reserved[2];
+};
+static_assert(sizeof(StateHeader) == 96, "state header layout");
+constexpr char kStateMagic[8] = {'C', 'C', 'P', 'M', 'S', 'T', 'A', 'T'};
+constexpr uint32_t kStateVersion = 1;
+
+size_t state_payload_bytes(int64_t n, int64_t words, size_t n_phases) {
+    return sizeof(ccpm_counts) + sizeof(int32_t) * n_phases + sizeof(uint32_t) * (size_t)(n + words);
+}
+}  // namespace
+
+int ccpm_state_export(ccpm_result_t r, void *buf, size_t *len) {
+    if (!r || !len) return CCPM_EINVAL;
+    ccpm_graph *g = r->g;
+    ccpm_ctx *ctx = g->ctx;
+    const int64_t words = (g->m + 31) / 32;
+    const size_t payload = state_payload_bytes(g->n, words, r->phase_rounds.size());
+    const size_t need = sizeof(StateHeader) + payload;
+    if (!buf) { *len = need; return CCPM_OK; }
+    if (*len < need) {
+        *len = need;
+        return set_err(ctx, CCPM_EINVAL, "state buffer too small");
+    }
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = kStateVersion;
+    h.header_bytes = sizeof(StateHeader);
+    h.n = g->n;
+    h.m_dir = g->m;
+    h.words = words;
+    h.graph_fp = graph_fingerprint(*g);
+    h.tmpl_fp = r->tmpl_fp;
+    h.counts_bytes = sizeof(ccpm_counts);
+    h.n_phases = (uint32_t)r->phase_rounds.size();
+    h.payload_bytes = payload;
+    unsigned char *p = (unsigned char *)buf + sizeof(StateHeader);
+    std::memcpy(p, &r->counts, sizeof(ccpm_counts));
+    p += sizeof(ccpm_counts);
+    if (!r->phase_rounds.empty()) std::memcpy(p, r->phase_rounds.data(), sizeof(int32_t) * r->phase_rounds.size());
+    p += sizeof(int32_t) * r->phase_rounds.size();
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaMemcpy(p, r->om, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost));
+    p += sizeof(uint32_t) * (size_t)g->n;
+    CU(ctx, cudaMemcpy(p, r->eb, sizeof(uint32_t) * (size_t)words, cudaMemcpyDeviceToHost));
+    h.payload_fnv = fnv1a((const unsigned char *)buf + sizeof(StateHeader), payload);
+    std::memcpy(buf, &h, sizeof(h));
+    *len = need;
+    return CCPM_OK;
+}
+
+int ccpm_state_import(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const void *buf, size_t len,
+                      ccpm_result_t *out) {
+    if (!ctx || !g || !tm || !buf || !out) return CCPM_EINVAL;
+    *out = nullptr;
+    if (g->ctx->device != ctx->device) return set_err(ctx, CCPM_EINVAL, "graph lives on another device");
+    StateHeader h;
+    if (len < sizeof(h)) return set_err(ctx, CCPM_EINVAL, "state: truncated header");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion ||
+        h.header_bytes != sizeof(StateHeader) || h.counts_bytes != sizeof(ccpm_counts))
+        return set_err(ctx, CCPM_EINVAL, "state: not a saved state of this library version");
+    const int64_t words = (g->m + 31) / 32;
+    if (h.n != g->n || h.m_dir != g->m || h.words != words || h.graph_fp != graph_fingerprint(*g))
+        return set_err(ctx, CCPM_EINVAL, "state: saved for another graph");
+    if (h.tmpl_fp != tmpl_fingerprint(tm->t)) return set_err(ctx, CCPM_EINVAL, "state: saved for another template");
+    if (h.n_phases > (1u << 20)) return set_err(ctx, CCPM_EINVAL, "state: bad phase count");
+    const size_t payload = state_payload_bytes(g->n, words, h.n_phases);
+    if (h.payload_bytes != payload || len < sizeof(h) + payload) return set_err(ctx, CCPM_EINVAL, "state: truncated");
+    const unsigned char *p = (const unsigned char *)buf + sizeof(h);
+    if (fnv1a(p, payload) != h.payload_fnv) return set_err(ctx, CCPM_EINVAL, "state: checksum mismatch");
+    CU(ctx, cudaSetDevice(ctx->device));
+    ccpm_result *r = new (std::nothrow) ccpm_result();
+    if (!r) return set_err(ctx, CCPM_ENOMEM, "result: host allocation");
+    r->g = g;
+    r->tmpl_fp = h.tmpl_fp;
+    int rc = dalloc(ctx, &r->om, (size_t)g->n);
+    if (!rc) rc = dalloc(ctx, &r->eb, (size_t)words + 1);
+    if (rc) {
+        cudaFree(r->om); cudaFree(r->eb);
+        delete r;
+        return rc;
+    }
+    std::memcpy(&r->counts, p, sizeof(ccpm_counts));
+    p += sizeof(ccpm_counts);
+    r->phase_rounds.resize(h.n_phases);
+    if (h.n_phases) std::memcpy(r->phase_rounds.data(), p, sizeof(int32_t) * h.n_phases);
+    p += sizeof(int32_t) * h.n_phases;
+    cudaError_t e = cudaMemcpy(r->om, p, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyHostToDevice);
+    p += sizeof(uint32_t) * (size_t)g->n;
+    if (e == cudaSuccess) e = cudaMemcpy(r->eb, p, sizeof(uint32_t) * (size_t)words, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(r->eb + words, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaFree(r->om); cudaFree(r->eb);
+        delete r;
+        return set_err(ctx, CCPM_ECUDA, std::string("state import: ") + cudaGetErrorString(e));
+    }
+    *out = r;
+    return CCPM_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -2639,7 +2801,8 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         NA_CU(cudaMemsetAsync(ebits, 0xFF, sizeof(uint32_t) * (size_t)words, s));
         if (m_dir & 31) k_set_word<<<1, 1, 0, s>>>(ebits + words - 1, (1u << (uint32_t)(m_dir & 31)) - 1u);
     }
-    k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, om[0], om[1], small[0], med[0], chunk[0], st, hub);
+    k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, nullptr, om[0], om[1], small[0], med[0], chunk[0], st,
+                                        hub);
     NA_CU(cudaGetLastError());
     NA_CU(read_stats());
     if (hs.n_hub_slots > (unsigned)L.acc_cap || (int64_t)hs.n_chunk > L.chunk_cap)
