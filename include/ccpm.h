@@ -104,7 +104,11 @@ typedef struct {
                                    /* *out (a result of this graph and template,  */
                                    /* e.g. one read back by ccpm_state_import)     */
                                    /* instead of from the initial state of Alg. 3  */
-    int      reserved[6];
+    int      compact;              /* row compaction between LCC rounds: 0 = when  */
+                                   /* most entries of the live rows are inactive,  */
+                                   /* 1 = after every round that leaves some, -1 = */
+                                   /* never; results are the same in all modes     */
+    int      reserved[5];
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 
@@ -149,6 +153,7 @@ typedef struct {
     int64_t  lcc_row_entries;      /* CSR entries in rows of active vertices  */
     int64_t  lcc_active_vertices;  /* active vertices, summed over rounds      */
     int64_t  kernel_launches;      /* all kernels this call launched          */
+    int64_t  lcc_compactions;      /* row compactions (K4) between LCC rounds */
 } ccpm_counts;
 
 /* ---------------------------------------------------------------- context */

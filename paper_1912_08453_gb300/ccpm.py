@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
     _fields_ = [("order_mode", ctypes.c_int), ("run_final", ctypes.c_int),
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6),
+                ("compact", ctypes.c_int), ("reserved", ctypes.c_int * 5),
                 ("mlp", ctypes.c_void_p)]
 
 
@@ -52,7 +52,8 @@ class Counts(ctypes.Structure):
                 ("ms_lcc", ctypes.c_double), ("ms_nlcc", ctypes.c_double), ("ms_final", ctypes.c_double),
                 ("lcc_launches", ctypes.c_int64), ("ms_lcc_kernel", ctypes.c_double),
                 ("lcc_alg_bytes", ctypes.c_int64), ("lcc_row_entries", ctypes.c_int64),
-                ("lcc_active_vertices", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("lcc_active_vertices", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("lcc_compactions", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

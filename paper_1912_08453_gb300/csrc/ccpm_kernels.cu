@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_sort.cuh>
 
 #include <atomic>
@@ -47,6 +48,8 @@ struct RoundStats {
     unsigned long long tokens;    // NLCC: (vertex, head) searches issued
     unsigned long long row_entries;   // CSR entries in rows of active vertices
     unsigned long long alive;         // active vertices processed
+    unsigned long long kept;          // entries still active after the round (rows of survivors)
+    unsigned long long rows_next;     // CSR entries in the rows of the survivors
     unsigned int changed;         // any omega or edge changed
     unsigned int n_small, n_med, n_chunk;   // next frontier sizes
     unsigned int n_hub_slots;
@@ -59,6 +62,7 @@ struct RoundStats {
 struct HubAcc {                   // partial LCC state of one split row
     uint32_t U, nN, flags, done;
     uint32_t cnt[kMaxCls];
+    uint32_t pbase;               // index of the row's first piece when the pieces were made
 };
 
 struct ChunkItem {                // one piece of a long row
@@ -167,7 +171,7 @@ struct LabelMask { uint32_t m[256]; };
 __global__ void __launch_bounds__(256)
 k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ lab, LabelMask lm,
        const uint32_t *__restrict__ om_in, uint32_t *om0, uint32_t *om1, int32_t *small_out, int32_t *med_out,
-       ChunkItem *chunk_out, RoundStats *st, int hub_deg) {
+       ChunkItem *chunk_out, HubAcc *acc, RoundStats *st, int hub_deg) {
     __shared__ uint32_t slm[256];
     __shared__ int32_t sbuf[2][8][32];
     __shared__ int scnt[2][8];
@@ -199,6 +203,7 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
             int nch = (int)((deg + hub_deg - 1) / hub_deg);
             int slot = (int)atomicAdd(&st->n_hub_slots, 1u);
             unsigned int base = atomicAdd(&st->n_chunk, (unsigned int)nch);
+            acc[slot].pbase = base;
             for (int c = 0; c < nch; c++) chunk_out[base + c] = ChunkItem{(int32_t)v, c, slot, nch};
         }
     }
@@ -226,6 +231,7 @@ struct LccArgs {
     HubAcc *acc;
     RoundStats *st;
     int hub_deg;
+    int64_t *deg;                 // entries each listed vertex keeps (0 if it dies), or nullptr
     int med_chunk;                // medium vertices a warp prefetches together (1..16)
     int small_chunk;              // short-row vertices a warp prefetches together (8, 16 or 32)
 };
@@ -291,36 +297,52 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
     load_step(0);
     for (int k0 = 0; k0 < nwin; k0 += UNR) {
         uint32_t wu[UNR];
+        bool was[UNR];
 #pragma unroll
-        for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+        for (int j = 0; j < UNR; j++) {
+            was[j] = act[j];
+            wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+        }
         if (k0 + UNR < nwin) load_step(k0 + UNR);
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             const uint32_t w = wu[j];
-            bool fail = false;
+            bool keep = false;
             if (w) {
                 scanned++;
                 if (w & nbr_v) {
+                    keep = true;
                     p.U |= w;
                     p.nN++;
 #pragma unroll
                     for (int c = 0; c < MAXC; c++)
                         if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
                 } else {
-                    fail = true;
+                    p.achg = 1u;            // eta eliminates the entry
                 }
             }
-            const uint32_t clr = __ballot_sync(FULL_MASK, fail);
-            if (clr) {
-                p.achg = 1u;
-                if (lane == 0) atomicAnd(&eb[k0 + j], ~clr);
+            // the bit goes with the failing entries and with those whose other
+            // end is already inactive (no change of the state A: that entry is
+            // inactive already), so later rounds and compaction see only live
+            // compatible entries
+            const uint32_t drop = __ballot_sync(FULL_MASK, was[j] && !keep);
+            if (drop) {
+                const int k = k0 + j;
+                if (k * 32 >= lo && k * 32 + 32 <= hi) {
+                    // the word holds entries of this row only
+                    const uint32_t kept = __ballot_sync(FULL_MASK, keep);
+                    if (lane == 0) eb[k] = kept;
+                } else if (lane == 0) {
+                    atomicAnd(&eb[k], ~drop);
+                }
             }
         }
     }
 }
 
 // Group form for rows of at most 32 entries: G lanes share a row; failing
-// entries are collected as a row-relative mask and cleared once per row.
+// entries, and those whose other end is inactive, are collected as a
+// row-relative mask and cleared once per row.
 template <int G, int MAXC, bool DENSE>
 __device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uint32_t nbr_v, int lane_g,
                                                    const int32_t *__restrict__ col,
@@ -350,7 +372,11 @@ __device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uin
 #pragma unroll
     for (int j = 0; j < UNR; j++) {
         const uint32_t w = wu[j];
-        if (!w) continue;
+        if (!w) {
+            // other end already inactive: drop the bit (no change of the state)
+            if (act[j]) clr |= 1u << (uint32_t)(lane_g + j * G);
+            continue;
+        }
         scanned++;
         if (w & nbr_v) {
             p.U |= w;
@@ -359,6 +385,7 @@ __device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uin
             for (int c = 0; c < MAXC; c++)
                 if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
         } else {
+            p.achg = 1u;
             clr |= 1u << (uint32_t)(lane_g + j * G);
         }
     }
@@ -414,7 +441,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t scanned = 0;          // per lane: at most one entry per window
-    unsigned long long rows = 0, alive = 0;
+    unsigned long long rows = 0, alive = 0, kept = 0, rows_next = 0;
     uint32_t changed = 0;
 
     // (1) pieces of long rows: one warp per piece, combined through HubAcc;
@@ -423,7 +450,10 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         ChunkItem ci = a.chunk_in[it];
         const uint32_t wv = __ldg(a.om_cur + ci.v);
         if (wv == 0u) {
-            if (ci.c == 0 && lane == 0) a.om_next[ci.v] = 0u;
+            if (ci.c == 0 && lane == 0) {
+                a.om_next[ci.v] = 0u;
+                if (a.deg) a.deg[ci.v] = 0;
+            }
             continue;
         }
         const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
@@ -459,7 +489,11 @@ k_lcc_round(LccArgs a, DevTmpl t) {
 #pragma unroll
             for (int c = 0; c < MAXC; c++) tot.cnt[c] = atomicAdd(&h->cnt[c], 0u);
             uint32_t keep = decide<MAXC>(wv, tot, s);
-            if (lane == 0) a.om_next[ci.v] = keep;
+            if (lane == 0) {
+                a.om_next[ci.v] = keep;
+                if (a.deg) a.deg[ci.v] = keep ? (int64_t)tot.nN : 0;
+            }
+            if (lane == 0 && keep) { kept += tot.nN; rows_next += (unsigned long long)(rend - rbeg); }
             if (keep != wv || tot.achg) changed = 1u;
             if (keep == 0u) clear_row<32>(a.ebits, rbeg, rend, lane);
             __syncwarp();
@@ -491,7 +525,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             if (v < 0) break;
             const uint32_t wv = __shfl_sync(FULL_MASK, wl, j);
             const int64_t beg = __shfl_sync(FULL_MASK, bl, j), end = __shfl_sync(FULL_MASK, el, j);
-            uint32_t keep = 0u;
+            uint32_t keep = 0u, p_nN = 0u;
             if (wv) {
                 if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
                 Partial<MAXC> p;
@@ -502,10 +536,15 @@ k_lcc_round(LccArgs a, DevTmpl t) {
 #pragma unroll
                 for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
                 keep = decide<MAXC>(wv, p, s);
+                p_nN = p.nN;
+                if (lane == 0 && keep) { kept += p.nN; rows_next += (unsigned long long)(end - beg); }
                 if (keep != wv || p.achg) changed = 1u;
                 if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
             }
-            if (lane == 0) a.om_next[v] = keep;
+            if (lane == 0) {
+                a.om_next[v] = keep;
+                if (a.deg) a.deg[v] = keep ? (int64_t)p_nN : 0;
+            }
             bm.push(lane == 0 && wv != 0u, v);
         }
     }
@@ -535,16 +574,20 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             uint32_t clr = scan_row_group<4, MAXC, DENSE>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits,
                                                           s, p, scanned);
             clr = grp_or<4>(clr);
-            p.achg = clr ? 1u : 0u;
+            p.achg = grp_or<4>(p.achg);
             if (lg == 0 && wv) clear_rel(a.ebits, beg, clr);
             p.U = grp_or<4>(p.U);
             p.nN = grp_sum<4>(p.nN);
 #pragma unroll
             for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<4>(p.cnt[c]);
             uint32_t keep = wv ? decide<MAXC>(wv, p, s) : 0u;
+            if (lg == 0 && keep) { kept += p.nN; rows_next += (unsigned long long)(end - beg); }
             if (wv && (keep != wv || p.achg)) changed = 1u;
             if (wv && keep == 0u) clear_row<4>(a.ebits, beg, end, lg);
-            if (v >= 0 && lg == 0) a.om_next[v] = keep;
+            if (v >= 0 && lg == 0) {
+                a.om_next[v] = keep;
+                if (a.deg) a.deg[v] = keep ? (int64_t)p.nN : 0;
+            }
             bs.push(lg == 0 && wv != 0u, v);
         }
     }
@@ -558,13 +601,312 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         scanned64 += __shfl_xor_sync(FULL_MASK, scanned64, o);
         rows += __shfl_xor_sync(FULL_MASK, rows, o);
         alive += __shfl_xor_sync(FULL_MASK, alive, o);
+        kept += __shfl_xor_sync(FULL_MASK, kept, o);
+        rows_next += __shfl_xor_sync(FULL_MASK, rows_next, o);
         changed |= __shfl_xor_sync(FULL_MASK, changed, o);
     }
     if (lane == 0) {
         if (scanned64) atomicAdd(&a.st->scanned, scanned64);
         if (rows) atomicAdd(&a.st->row_entries, rows);
         if (alive) atomicAdd(&a.st->alive, alive);
+        if (kept) atomicAdd(&a.st->kept, kept);
+        if (rows_next) atomicAdd(&a.st->rows_next, rows_next);
         if (changed) atomicOr(&a.st->changed, 1u);
+    }
+}
+
+// -------------------------------------------------------------------------
+// K4: row compaction between LCC rounds (frontier and edge-bitmap compaction)
+//
+// Later rounds touch only the survivors, but the rows of the survivors still
+// hold every neighbour they started with; once most of those entries are
+// inactive a round spends its time skipping them.  Compaction writes a new
+// CSR whose rows keep, in the same (ascending id) order, only the entries
+// whose bit is set and whose other end point is still active: exactly the
+// entries the next round would examine.  Ids stay the original vertex ids;
+// the new bitmap starts with every bit set.  Entries left out are inactive
+// for good (bits are only ever cleared and omega only shrinks), so every
+// later round, and every search at a fixpoint, sees the same active entries
+// as on the full rows.
+//
+// The frontier is rebuilt first (k_init over the live vertices) so that the
+// pieces of a long row are consecutive in the piece list, in piece order:
+// piece c's output offset is then the row's offset plus the counts of pieces
+// 0..c-1.
+// -------------------------------------------------------------------------
+
+struct CompactArgs {
+    const int64_t *rp;            // rows being compacted
+    const int32_t *col;
+    const uint32_t *bits;         // set exactly for the entries to keep
+    const uint8_t *lab;
+    const uint32_t *om;           // omega after the last round
+    const int32_t *small_in;
+    const int32_t *med_in;
+    const ChunkItem *chunk_in;
+    const HubAcc *acc;            // first-piece index of each long row (pbase)
+    int64_t n_small, n_med, n_chunk;
+    int hub_deg;
+    int n_rank;                   // distinct labels of the template
+    uint8_t lab_rank[256];        // rank of a template label among them
+    uint8_t rank_label[kMaxT];
+    uint32_t *piece_cnt;          // kept entries per (piece, rank) of long rows
+    const int64_t *sub_rp;        // offsets of the new rows
+    int32_t *sub_col;             // the new rows, grouped by label, ids ascending
+    uint8_t *sub_nlab;            // inside a group, and their labels
+};
+
+// Position of the r-th (0-based) set bit of x (x has more than r set bits):
+// halve the range, keeping the half that holds it.
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t w = 16; w > 0; w >>= 1) {
+        const uint32_t low = __popc(x & ((1u << w) - 1u));
+        if (low <= r) { r -= low; x >>= w; pos += w; }
+    }
+    return pos;
+}
+
+// Visit the entries of [beg, end) whose bit is set, 32 at a time and in
+// ascending order: f(e, valid) is called by all lanes, lane i with the i-th
+// set entry of the batch (valid) or none.  The bits are read 32 words
+// (1024 entries) per load, so long runs of inactive entries cost little.
+template <typename F>
+__device__ __forceinline__ void for_set_bits(const uint32_t *bits, int64_t beg, int64_t end, F &&f) {
+    const int lane = (int)lane_id();
+    const int64_t wb = beg >> 5, we = (end + 31) >> 5;
+    for (int64_t w0 = wb; w0 < we; w0 += 32) {
+        const int64_t wi = w0 + lane;
+        uint32_t word = 0u;
+        if (wi < we) {
+            word = bits[wi];
+            const int64_t e0 = wi << 5;
+            if (e0 < beg) word &= ~0u << (uint32_t)(beg - e0);
+            if (end - e0 < 32) word &= (1u << (uint32_t)(end - e0)) - 1u;
+        }
+        const uint32_t c = __popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        const uint32_t excl = incl - c;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t k = k0 + (uint32_t)lane;
+            int i = 0;                                // last word whose prefix is <= k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t ex = __shfl_sync(FULL_MASK, excl, i + step);
+                if (ex <= k) i += step;
+            }
+            const uint32_t wd = __shfl_sync(FULL_MASK, word, i);
+            const uint32_t ex_i = __shfl_sync(FULL_MASK, excl, i);
+            const bool valid = k < total;
+            int64_t e = -1;
+            if (valid) e = ((w0 + i) << 5) + (int64_t)select_bit(wd, k - ex_i);
+            f(e, valid);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lane_rank_count(int r, int n_rank) {
+    uint32_t rc = 0;
+    for (int rr = 0; rr < n_rank; rr++) {
+        const uint32_t m = __ballot_sync(FULL_MASK, r == rr);
+        if ((int)lane_id() == rr) rc = __popc(m);
+    }
+    return rc;
+}
+
+// Kept entries of [beg, end) per label rank, summed into lane r (r < n_rank).
+__device__ __forceinline__ uint32_t rank_counts(const CompactArgs &a, int64_t beg, int64_t end) {
+    uint32_t rc = 0;
+    for_set_bits(a.bits, beg, end, [&](int64_t e, bool valid) {
+        int r = valid ? (int)a.lab_rank[__ldg(a.lab + __ldg(a.col + e))] : -1;
+        if (r >= a.n_rank) r = -1;           // never: kept entries have template labels
+        rc += lane_rank_count(r, a.n_rank);
+    });
+    return rc;
+}
+
+// Write the kept entries of [beg, end): lane r holds the next output index of
+// label rank r.  Order inside a rank is the visiting order (ascending).
+__device__ __forceinline__ void place_ranked(const CompactArgs &a, int64_t beg, int64_t end, int64_t cur) {
+    const int lane = (int)lane_id();
+    const uint32_t below = (1u << lane) - 1u;
+    for_set_bits(a.bits, beg, end, [&](int64_t e, bool valid) {
+        int32_t u = -1;
+        int r = -1;
+        if (valid) {
+            u = __ldg(a.col + e);
+            r = (int)a.lab_rank[__ldg(a.lab + u)];
+            if (r >= a.n_rank) r = -1;
+        }
+        int64_t pos = -1;
+        for (int rr = 0; rr < a.n_rank; rr++) {
+            const uint32_t m = __ballot_sync(FULL_MASK, r == rr);
+            const int64_t base = __shfl_sync(FULL_MASK, cur, rr);
+            if (r == rr) pos = base + __popc(m & below);
+            if (lane == rr) cur += __popc(m);
+        }
+        if (r >= 0) {
+            a.sub_col[pos] = u;
+            a.sub_nlab[pos] = a.rank_label[r];
+        }
+    });
+}
+
+// Exclusive prefix over lanes.
+__device__ __forceinline__ uint32_t lane_excl(uint32_t x) {
+    const int lane = (int)lane_id();
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    return incl - x;
+}
+
+// Per-(piece, rank) kept entries of the pieces of long rows.
+__global__ void __launch_bounds__(256)
+k_compact_count(CompactArgs a) {
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+        const ChunkItem ci = a.chunk_in[it];
+        if (__ldg(a.om + ci.v) == 0u) continue;
+        const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
+        const int64_t beg = rbeg + (int64_t)ci.c * a.hub_deg;
+        const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
+        const uint32_t rc = rank_counts(a, beg, end);
+        const int64_t p = (int64_t)a.acc[ci.slot].pbase + ci.c;
+        if (lane < a.n_rank) a.piece_cnt[p * a.n_rank + lane] = rc;
+    }
+}
+
+// Write the new rows.  Pieces of long rows: rank r's group starts after the
+// lower ranks of the whole row, and a piece's entries of rank r follow those
+// of the row's earlier pieces.  Whole rows: one pass when the row keeps at
+// most 32 entries (a warp-wide stable sort by rank), else count then place.
+__global__ void __launch_bounds__(256)
+k_compact_fill(CompactArgs a) {
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    const uint32_t below = (1u << lane) - 1u;
+    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+        const ChunkItem ci = a.chunk_in[it];
+        if (__ldg(a.om + ci.v) == 0u) continue;
+        const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
+        const int64_t beg = rbeg + (int64_t)ci.c * a.hub_deg;
+        const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
+        const int64_t p0 = (int64_t)a.acc[ci.slot].pbase;
+        uint32_t tot = 0, before = 0;
+        if (lane < a.n_rank) {
+            for (int c2 = 0; c2 < ci.nchunks; c2++) {
+                const uint32_t x = a.piece_cnt[(p0 + c2) * a.n_rank + lane];
+                tot += x;
+                if (c2 < ci.c) before += x;
+            }
+        }
+        place_ranked(a, beg, end, a.sub_rp[ci.v] + (int64_t)lane_excl(tot) + before);
+    }
+    // whole rows, 32 list entries per warp step.  A row keeping at most 16
+    // entries (most of them, once the first round has run) is written by its
+    // own lane, one pass per label rank; the others by the whole warp in turn.
+    const int64_t n_rows = a.n_med + a.n_small;
+    for (int64_t b = gwarp * 32; b < n_rows; b += nwarps * 32) {
+        const int64_t idx = b + lane;
+        int32_t vl = -1;
+        int64_t beg = 0, end = 0, out = 0, k = 0;
+        if (idx < n_rows) {
+            vl = idx < a.n_med ? a.med_in[idx] : a.small_in[idx - a.n_med];
+            if (__ldg(a.om + vl) == 0u) vl = -1;
+        }
+        if (vl >= 0) {
+            beg = a.rp[vl];
+            end = a.rp[vl + 1];
+            out = a.sub_rp[vl];
+            k = a.sub_rp[vl + 1] - out;
+        }
+        if (vl >= 0 && k > 0 && k <= 16) {
+            const int64_t stop = out + k;
+            for (int r = 0; r < a.n_rank && out < stop; r++) {
+                const uint8_t L = a.rank_label[r];
+                for (int64_t wi = beg >> 5; (wi << 5) < end && out < stop; wi++) {
+                    uint32_t word = a.bits[wi];
+                    const int64_t e0 = wi << 5;
+                    if (e0 < beg) word &= ~0u << (uint32_t)(beg - e0);
+                    if (end - e0 < 32) word &= (1u << (uint32_t)(end - e0)) - 1u;
+                    for (; word; word &= word - 1u) {
+                        const int32_t u = __ldg(a.col + e0 + __ffs(word) - 1);
+                        if (__ldg(a.lab + u) == L && out < stop) {
+                            a.sub_col[out] = u;
+                            a.sub_nlab[out] = L;
+                            out++;
+                        }
+                    }
+                }
+            }
+        }
+        for (uint32_t big = __ballot_sync(FULL_MASK, vl >= 0 && k > 16); big; big &= big - 1u) {
+            const int src = __ffs(big) - 1;
+            const int64_t rb = __shfl_sync(FULL_MASK, beg, src), re = __shfl_sync(FULL_MASK, end, src);
+            const int64_t ro = __shfl_sync(FULL_MASK, out, src);
+            const uint32_t rc = rank_counts(a, rb, re);
+            place_ranked(a, rb, re, ro + (int64_t)lane_excl(lane < a.n_rank ? rc : 0u));
+        }
+    }
+}
+
+// Bits of the compacted rows: every entry active, nothing past the last one.
+__global__ void k_compact_bits(uint32_t *bits, const int64_t *total) {
+    const int64_t m2 = *total;
+    const int64_t words = (m2 + 31) / 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= words; i += stride) {
+        uint32_t v = 0u;
+        if (i < words) v = (i == words - 1 && (m2 & 31)) ? (1u << (uint32_t)(m2 & 31)) - 1u : ~0u;
+        bits[i] = v;
+    }
+}
+
+// Edge map of the final state when it is handed back without the final
+// search: at an LCC fixpoint an entry between two active vertices is active
+// iff their omegas are compatible (eta); entries cleared earlier stay
+// cleared.  One warp per vertex, over the full rows.
+__global__ void __launch_bounds__(256)
+k_materialize_fix(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restrict__ rp,
+                  const int32_t *__restrict__ col, uint32_t *ebits, DevTmpl t) {
+    __shared__ uint32_t sadj[kMaxT];
+    for (int i = threadIdx.x; i < kMaxT; i += blockDim.x) sadj[i] = t.adj[i];
+    __syncthreads();
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t v = gwarp; v < n; v += nwarps) {
+        const int64_t beg = rp[v], end = rp[v + 1];
+        if (beg == end) continue;
+        const uint32_t wv = om[v];
+        if (wv == 0u) {
+            clear_row<32>(ebits, beg, end, lane);
+            continue;
+        }
+        uint32_t nb = 0;
+        for (uint32_t x = wv; x; x &= x - 1u) nb |= sadj[__ffs(x) - 1];
+        for (int64_t w0 = beg >> 5; (w0 << 5) < end; w0++) {
+            const int64_t e = (w0 << 5) + lane;
+            const uint32_t word = ebits[w0];
+            bool drop = false;
+            if (e >= beg && e < end && ((word >> lane) & 1u)) drop = (__ldg(om + __ldg(col + e)) & nb) == 0u;
+            const uint32_t dm = __ballot_sync(FULL_MASK, drop);
+            if (dm && lane == 0) atomicAnd(&ebits[w0], ~dm);
+        }
     }
 }
 
@@ -594,8 +936,10 @@ struct __align__(16) SearchItem {
 struct SearchArgs {
     const int64_t *rp;
     const int32_t *col;       // id-sorted rows (edge-bitmap indexing)
-    const int32_t *lcol;      // rows grouped by neighbour label, ids ascending inside a group
-    const uint8_t *nlab;      // label of lcol[e]
+    const int64_t *rl;        // offsets of the rows the searches scan:
+    const int32_t *lcol;      // the full rows grouped by neighbour label, ids ascending
+    const uint8_t *nlab;      // inside a group, with nlab = label of lcol[e]; or
+                              // compacted rows (ids ascending) with nlab = nullptr
     const uint32_t *om;
     const int32_t *roots;
     int64_t n_roots;
@@ -627,10 +971,17 @@ struct WarpSearch {
     int64_t blo[kMaxT][kMaxBack], bhi[kMaxT][kMaxBack];
 };
 
-// [lo, hi) of the label-L group in the label-grouped row of x.
+// [lo, hi) of the label-L group in the label-grouped row of x; the whole row
+// when the rows are compacted ones (nlab == nullptr: ids ascending, every
+// label mixed; candidates are then told apart by their omega alone).
 __device__ __forceinline__ void label_range(const int64_t *rp, const uint8_t *nlab, int32_t x, uint32_t L,
                                             int64_t &lo, int64_t &hi) {
     const int64_t a = rp[x], b = rp[x + 1];
+    if (nlab == nullptr) {
+        lo = a;
+        hi = b;
+        return;
+    }
     int64_t l = a, h = b;
     while (l < h) {
         int64_t m = (l + h) >> 1;
@@ -648,7 +999,7 @@ __device__ __forceinline__ void label_range(const int64_t *rp, const uint8_t *nl
 // Is u (label L) a neighbour of x?  Binary search inside x's label-L group.
 __device__ __forceinline__ bool adjacent(const SearchArgs &a, int32_t x, int32_t u, uint32_t L) {
     int64_t lo, hi;
-    label_range(a.rp, a.nlab, x, L, lo, hi);
+    label_range(a.rl, a.nlab, x, L, lo, hi);
     const int64_t stop = hi;
     while (lo < hi) {
         int64_t m = (lo + hi) >> 1;
@@ -680,7 +1031,7 @@ __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P
         uint32_t m = cm;
         for (int i = 0; i < lane; i++) m &= m - 1u;
         j = __ffs(m) - 1;
-        label_range(a.rp, a.nlab, W.psi[j], P.lab[d], lo, hi);
+        label_range(a.rl, a.nlab, W.psi[j], P.lab[d], lo, hi);
         len = hi - lo;
     }
     int best = lane;
@@ -915,7 +1266,7 @@ k_expand(SearchArgs a) {
             const DevPlan &P = a.plans[a.enum_heads ? 0 : h];
             const int q1 = P.q[1];
             int64_t lo, hi;
-            label_range(a.rp, a.nlab, v, P.lab[1], lo, hi);
+            label_range(a.rl, a.nlab, v, P.lab[1], lo, hi);
             entries += (unsigned long long)(hi - lo);
             for (int64_t base = lo; base < hi; base += 32) {
                 const int64_t e = base + lane;
@@ -1328,6 +1679,17 @@ struct Workspace {
     unsigned long long *hist_h = nullptr;
     DevPlan *plans_h = nullptr;      // pinned staging for plan uploads
     cudaEvent_t ev[10] = {};
+    // compacted rows (K4), two generations; allocated at the first compaction
+    int64_t *sub_rp[2] = {nullptr, nullptr};
+    int32_t *sub_col[2] = {nullptr, nullptr};
+    uint32_t *sub_bits[2] = {nullptr, nullptr};
+    int64_t sub_cap[2] = {0, 0};     // entries sub_col / sub_bits can hold
+    int64_t *deg = nullptr;          // n + 1 kept-entry counts, scanned into sub_rp
+    uint8_t *sub_nlab[2] = {nullptr, nullptr};
+    uint32_t *piece_cnt = nullptr;   // kept entries per (piece, label rank) of long rows
+    int64_t piece_cap = 0;
+    void *scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
 };
 
 struct ccpm_ctx {
@@ -1431,6 +1793,9 @@ void ws_free(Workspace &w) {
     if (w.hist_h) cudaFreeHost(w.hist_h);
     if (w.plans_h) cudaFreeHost(w.plans_h);
     for (auto &e : w.ev) if (e) cudaEventDestroy(e);
+    for (int i = 0; i < 2; i++) { cudaFree(w.sub_rp[i]); cudaFree(w.sub_col[i]); cudaFree(w.sub_bits[i]); }
+    for (int i = 0; i < 2; i++) cudaFree(w.sub_nlab[i]);
+    cudaFree(w.deg); cudaFree(w.piece_cnt); cudaFree(w.scan_tmp);
     w = Workspace{};
 }
 
@@ -1588,6 +1953,15 @@ struct Pipeline {
     int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
     double ms_lcc_kernel = 0.0;
     int maxc = 0;
+    // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
+    const int64_t *lrp = nullptr;
+    const int32_t *lcol = nullptr;
+    uint32_t *lbits = nullptr;
+    int gen = -1;                   // compacted generation in use, -1 = full rows
+    int compact_mode = 0;           // options.compact
+    int64_t compactions = 0;
+    const uint8_t *lnlab = nullptr; // labels of lcol (compacted rows are label-grouped)
+    int64_t last_kept = -1, last_rows = -1;   // the latest round: entries still active, rows of the survivors
 
     // alive counts per template vertex (w.hist_h[0..31]) and total bits ([32])
     int omega_hist() {
@@ -1612,11 +1986,11 @@ struct Pipeline {
     int launch_round() {
         Workspace &w = ctx->ws;
         LccArgs a;
-        a.rp = g->rp;
-        a.col = g->col;
+        a.rp = lrp;
+        a.col = lcol;
         a.om_cur = w.om[cur];
         a.om_next = w.om[cur ^ 1];
-        a.ebits = w.ebits;
+        a.ebits = lbits;
         a.small_in = w.small[li];
         a.med_in = w.med[li];
         a.chunk_in = w.chunk[li];
@@ -1629,6 +2003,7 @@ struct Pipeline {
         a.acc = w.acc;
         a.st = w.st;
         a.hub_deg = w.hub_deg;
+        a.deg = compact_mode >= 0 ? w.deg : nullptr;
         // prefetch units: large enough to hide the per-vertex loads, small
         // enough that every resident warp gets several of them
         const int64_t resident = (int64_t)ctx->num_sms * 32;
@@ -1675,13 +2050,145 @@ struct Pipeline {
             n_small = w.st_h->n_small;
             n_med = w.st_h->n_med;
             n_chunk = w.st_h->n_chunk;
+            last_kept = (int64_t)w.st_h->kept;
+            last_rows = (int64_t)w.st_h->rows_next;
             li ^= 1;
             cur ^= 1;
             if (!w.st_h->changed) break;
             if (r > (int64_t)4 * (g->m + g->n) + 8)
                 return set_err(ctx, CCPM_ETIMEOUT, "LCC did not converge");
+            if (want_compact() && (rc = compact())) return rc;
         }
         *rounds = r;
+        return CCPM_OK;
+    }
+
+    // Compact when most entries of the live rows are inactive: the next round
+    // (or search) would mostly skip them.
+    bool want_compact() const {
+        if (compact_mode < 0 || last_rows <= 0) return false;
+        if (compact_mode > 0) return last_kept < last_rows;
+        return last_rows >= ((int64_t)1 << 21) && last_kept * 8 < last_rows;
+    }
+
+    // Frontier of the live vertices over rows rp (the pieces of a long row
+    // consecutive and in order); also makes both omega buffers equal.
+    int rebucket(const int64_t *rp) {
+        Workspace &w = ctx->ws;
+        LabelMask all;
+        std::memset(&all, 0xFF, sizeof(all));
+        CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), ctx->stream));
+        launches++;
+        k_init<<<grid_for(ctx, g->n, 256, 8), 256, 0, ctx->stream>>>(g->n, rp, g->lab, all, w.om[cur], w.om[cur],
+                                                                     w.om[cur ^ 1], w.small[li], w.med[li],
+                                                                     w.chunk[li], w.acc, w.st, w.hub_deg);
+        CU(ctx, cudaGetLastError());
+        int rc = read_stats();
+        if (rc) return rc;
+        n_small = w.st_h->n_small;
+        n_med = w.st_h->n_med;
+        n_chunk = w.st_h->n_chunk;
+        if (w.st_h->n_hub_slots > (unsigned)w.acc_cap || n_chunk > w.chunk_cap)
+            return set_err(ctx, CCPM_EOVERFLOW, "hub bookkeeping overflow");
+        return CCPM_OK;
+    }
+
+    // K4: new rows holding only the entries the next round would examine,
+    // grouped by label (the searches scan label groups).  The kept entries
+    // are a subset of those the last round found compatible (last_kept), so
+    // the new arrays are sized before anything runs; one host sync at the end
+    // reads the new frontier sizes.
+    int compact() {
+        Workspace &w = ctx->ws;
+        cudaStream_t s = ctx->stream;
+        const int nb = gen < 0 ? 0 : (gen ^ 1);
+        int rc;
+        // label ranks of the template vertices
+        uint8_t labs[kMaxT];
+        int nl = 0;
+        for (int q = 0; q < t->n0; q++) labs[nl++] = t->labels[q];
+        std::sort(labs, labs + nl);
+        nl = (int)(std::unique(labs, labs + nl) - labs);
+        if (w.piece_cap < w.chunk_cap * nl) {
+            cudaFree(w.piece_cnt);
+            w.piece_cnt = nullptr;
+            w.piece_cap = 0;
+            if ((rc = dalloc(ctx, &w.piece_cnt, (size_t)(w.chunk_cap * kMaxT)))) return rc;
+            w.piece_cap = w.chunk_cap * kMaxT;
+        }
+        if (!w.sub_rp[nb] && (rc = dalloc(ctx, &w.sub_rp[nb], (size_t)g->n + 1))) return rc;
+        const int64_t need = last_kept + 64;
+        if (need > w.sub_cap[nb]) {
+            cudaFree(w.sub_col[nb]);
+            cudaFree(w.sub_nlab[nb]);
+            cudaFree(w.sub_bits[nb]);
+            w.sub_col[nb] = nullptr;
+            w.sub_nlab[nb] = nullptr;
+            w.sub_bits[nb] = nullptr;
+            w.sub_cap[nb] = 0;
+            const int64_t cap = std::max<int64_t>(need, w.sub_cap[nb ^ 1]);
+            if ((rc = dalloc(ctx, &w.sub_col[nb], (size_t)cap))) return rc;
+            if ((rc = dalloc(ctx, &w.sub_nlab[nb], (size_t)cap))) return rc;
+            if ((rc = dalloc(ctx, &w.sub_bits[nb], (size_t)(cap / 32 + 2)))) return rc;
+            w.sub_cap[nb] = cap;
+        }
+        CompactArgs ca{};
+        ca.rp = lrp;
+        ca.col = lcol;
+        ca.bits = lbits;
+        ca.lab = g->lab;
+        ca.om = w.om[cur];
+        ca.small_in = w.small[li];
+        ca.med_in = w.med[li];
+        ca.chunk_in = w.chunk[li];
+        ca.acc = w.acc;
+        ca.n_small = n_small;
+        ca.n_med = n_med;
+        ca.n_chunk = n_chunk;
+        ca.hub_deg = w.hub_deg;
+        ca.n_rank = nl;
+        std::memset(ca.lab_rank, 0xFF, sizeof(ca.lab_rank));
+        for (int r = 0; r < nl; r++) {
+            ca.lab_rank[labs[r]] = (uint8_t)r;
+            ca.rank_label[r] = labs[r];
+        }
+        ca.piece_cnt = w.piece_cnt;
+        // offsets of the new rows from the entries each vertex kept in the last
+        // round (0 for every vertex that is not live)
+        size_t tmp = 0;
+        CU(ctx, cub::DeviceScan::ExclusiveSum(nullptr, tmp, w.deg, w.sub_rp[nb], g->n + 1, s));
+        if (tmp > w.scan_tmp_bytes) {
+            cudaFree(w.scan_tmp);
+            w.scan_tmp = nullptr;
+            w.scan_tmp_bytes = 0;
+            CU(ctx, cudaMalloc(&w.scan_tmp, tmp));
+            w.scan_tmp_bytes = tmp;
+        }
+        launches++;
+        CU(ctx, cub::DeviceScan::ExclusiveSum(w.scan_tmp, tmp, w.deg, w.sub_rp[nb], g->n + 1, s));
+        if (n_chunk > 0) {
+            launches++;
+            k_compact_count<<<grid_for(ctx, n_chunk * 32, 256, 8), 256, 0, s>>>(ca);
+            CU(ctx, cudaGetLastError());
+        }
+        ca.sub_rp = w.sub_rp[nb];
+        ca.sub_col = w.sub_col[nb];
+        ca.sub_nlab = w.sub_nlab[nb];
+        launches++;
+        k_compact_fill<<<grid_for(ctx, n_chunk * 32 + n_med + n_small, 256, 8), 256, 0, s>>>(ca);
+        CU(ctx, cudaGetLastError());
+        launches++;
+        k_compact_bits<<<grid_for(ctx, last_kept / 32 + 2, 256, 8), 256, 0, s>>>(w.sub_bits[nb], w.sub_rp[nb] + g->n);
+        CU(ctx, cudaGetLastError());
+        lrp = w.sub_rp[nb];
+        lcol = w.sub_col[nb];
+        lnlab = w.sub_nlab[nb];
+        lbits = w.sub_bits[nb];
+        gen = nb;
+        dense = true;
+        compactions++;
+        if ((rc = rebucket(lrp))) return rc;
+        last_rows = last_kept;          // at most; every entry is now active
         return CCPM_OK;
     }
 };
@@ -1931,6 +2438,10 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.t = &t;
     build_dev_tmpl(t, P.dt);
     P.maxc = P.dt.n_cls;
+    P.lrp = g->rp;
+    P.lcol = g->col;
+    P.lbits = w.ebits;
+    P.compact_mode = opt.compact;
     cudaStream_t s = ctx->stream;
 
 #define CUF(call)                                                                       \
@@ -1947,6 +2458,12 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         if (rc_) return fail(rc_);    \
     } while (0)
 
+    if (P.compact_mode >= 0) {
+        // kept-entry counts the rounds leave for a compaction: 0 for every vertex
+        // no round has listed
+        if (!w.deg) RCF(dalloc(ctx, &w.deg, (size_t)g->n + 1));
+        CUF(cudaMemsetAsync(w.deg, 0, sizeof(int64_t) * (size_t)(g->n + 1), s));
+    }
     CUF(cudaEventRecord(w.ev[0], s));
     // ---- init (Alg. 3)
     LabelMask lm;
@@ -1973,7 +2490,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         P.launches++;
         k_init<<<grid, 256, 0, s>>>(g->n, g->rp, g->lab, lm, resume ? r->om : nullptr, w.om[0], w.om[1],
                                     w.small[0], w.med[0],
-                                    w.chunk[0], w.st, hub_deg);
+                                    w.chunk[0], w.acc, w.st, hub_deg);
         CUF(cudaGetLastError());
     }
     if (resume) {
@@ -2073,13 +2590,15 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         RCF(P.read_stats());
         const int64_t n_roots = w.st_h->n_roots;
         if (n_roots > 0) {
-            RCF(ensure_label_rows(ctx, g));
+            if (P.want_compact()) RCF(P.compact());
+            if (P.gen < 0) RCF(ensure_label_rows(ctx, g));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             SearchArgs a{};
             a.rp = g->rp;
             a.col = g->col;
-            a.lcol = g->lcol;
-            a.nlab = g->nlab;
+            a.rl = P.gen >= 0 ? P.lrp : g->rp;
+            a.lcol = P.gen >= 0 ? P.lcol : g->lcol;
+            a.nlab = P.gen >= 0 ? P.lnlab : g->nlab;
             a.om = w.om[P.cur];
             a.roots = w.roots;
             a.n_roots = n_roots;
@@ -2109,7 +2628,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             CUF(cudaGetLastError());
             P.launches++;
             k_nlcc_apply<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, c.hmask, w.sat,
-                                                                        w.om[0], w.om[1], g->rp, w.ebits, w.st);
+                                                                        w.om[0], w.om[1], P.lrp, P.lbits, w.st);
             CUF(cudaGetLastError());
             RCF(P.read_stats());
             if (w.st_h->overflow) over = true;
@@ -2148,14 +2667,16 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     bool final_done = false;
     if (opt.run_final) {
         const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
-        RCF(ensure_label_rows(ctx, g));
+        if (P.want_compact()) RCF(P.compact());
+        if (P.gen < 0) RCF(ensure_label_rows(ctx, g));
         CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
         CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
         SearchArgs a{};
         a.rp = g->rp;
         a.col = g->col;
-        a.lcol = g->lcol;
-        a.nlab = g->nlab;
+        a.rl = P.gen >= 0 ? P.lrp : g->rp;
+        a.lcol = P.gen >= 0 ? P.lcol : g->lcol;
+        a.nlab = P.gen >= 0 ? P.lnlab : g->nlab;
         a.roots = w.roots;
         a.next_root = w.next_root;
         a.plans = w.plans;
@@ -2321,7 +2842,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     if (!final_done) {
         // hand back the pruned state: exact edge map for live rows, dead rows zeroed
         P.launches++;
-        k_materialize<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, g->col, w.ebits);
+        k_materialize_fix<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, g->col,
+                                                                           w.ebits, P.dt);
         CUF(cudaGetLastError());
         CUF(cudaMemcpyAsync(r->om, w.om[P.cur], sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
         CUF(cudaMemcpyAsync(r->eb, w.ebits, sizeof(uint32_t) * (size_t)w.words, cudaMemcpyDeviceToDevice, s));
@@ -2361,6 +2883,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     cn.lcc_active_vertices = P.alive;
     cn.lcc_alg_bytes = 24 * P.alive + 4 * P.rows + P.rows / 8 + 4 * P.scanned;
     cn.kernel_launches = P.launches;
+    cn.lcc_compactions = P.compactions;
     int status = CCPM_OK;
     if (over || (opt.run_final && !count_valid)) status = CCPM_EBUDGET;
     cn.status = status;
@@ -2801,8 +3324,8 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         NA_CU(cudaMemsetAsync(ebits, 0xFF, sizeof(uint32_t) * (size_t)words, s));
         if (m_dir & 31) k_set_word<<<1, 1, 0, s>>>(ebits + words - 1, (1u << (uint32_t)(m_dir & 31)) - 1u);
     }
-    k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, nullptr, om[0], om[1], small[0], med[0], chunk[0], st,
-                                        hub);
+    k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, nullptr, om[0], om[1], small[0], med[0], chunk[0], acc,
+                                        st, hub);
     NA_CU(cudaGetLastError());
     NA_CU(read_stats());
     if (hs.n_hub_slots > (unsigned)L.acc_cap || (int64_t)hs.n_chunk > L.chunk_cap)
@@ -2830,6 +3353,7 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         a.acc = acc;
         a.st = st;
         a.hub_deg = hub;
+        a.deg = nullptr;
         a.med_chunk = 1;
         a.small_chunk = 8;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
