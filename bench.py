@@ -140,17 +140,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """Per-launch DRAM bytes of the LCC round kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"lcc_round_{workload}.md")
+def recorded_traffic(kernel, workload):
+    """Average DRAM bytes per launch of `kernel` over the timed step, from the
+    committed ncu summary, only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"dram_{workload}.md")
     if not os.path.exists(path):
         return None
     src, traffic = None, None
     for line in open(path):
         if line.startswith("kernel-source-sha256:"):
             src = line.split(":", 1)[1].strip()
-        if line.startswith("dram-bytes-per-launch:"):
+        if line.startswith(f"dram-bytes-per-launch {kernel}:"):
             traffic = float(line.split(":", 1)[1].strip())
     if src != kernel_source_hash():
         return None
@@ -373,17 +373,26 @@ def main():
     value = edges / (total_ms / 1e3)
     tts = {k: statistics.mean(st[k]["ms_total"] for st in agg) for k in tmpls}
 
-    # roofline of the dominant kernel: the LCC round
-    lcc_bytes = sum(c["lcc_alg_bytes"] for st in agg for c in st.values())
-    lcc_ms = sum(c["ms_lcc_kernel"] for st in agg for c in st.values())
-    lcc_launches = sum(c["lcc_launches"] for st in agg for c in st.values())
+    # rooflines of the two kernels that take the time: the LCC round (algorithmic
+    # bytes: 24 per active vertex, 4.125 per row entry, 4 per active entry) and
+    # the NLCC search (8 per row entry examined: the column index and the
+    # neighbour's omega); "roofline" is the one with more device time
     peak, peak_kind = measured_peak_hbm()
-    achieved = (lcc_bytes / 1e9) / (lcc_ms / 1e3) if lcc_ms > 0 else 0.0
-    traffic = recorded_traffic(args.workload)
-    roofline = {"bound": "hbm", "kernel": "k_lcc_round", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": traffic, "alg_bytes_per_launch": lcc_bytes / max(lcc_launches, 1),
-                "avg_launch_ms": lcc_ms / max(lcc_launches, 1), "launches": lcc_launches}
+
+    def roof(kernel, alg_bytes, ms, n_launch):
+        achieved = (alg_bytes / 1e9) / (ms / 1e3) if ms > 0 else 0.0
+        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": recorded_traffic(kernel, args.workload),
+                "alg_bytes_per_launch": alg_bytes / max(n_launch, 1),
+                "avg_launch_ms": ms / max(n_launch, 1), "launches": n_launch, "device_ms": ms}
+
+    every = [c for st in agg for c in st.values()]
+    roof_lcc = roof("k_lcc_round", sum(c["lcc_alg_bytes"] for c in every), sum(c["ms_lcc_kernel"] for c in every),
+                    sum(c["lcc_launches"] for c in every))
+    roof_search = roof("k_nlcc_items", 8 * sum(c["search_entries_nlcc"] for c in every),
+                       sum(c["ms_search_kernel"] for c in every), sum(c["search_launches"] for c in every))
+    roofline = roof_search if roof_search["device_ms"] > roof_lcc["device_ms"] else roof_lcc
     launches = sum(c["kernel_launches"] for st in agg for c in st.values())
 
     e2e = None
@@ -408,7 +417,8 @@ def main():
                 "tts_ms": tts,
                 "phases": {k: results[k].phase_rounds() for k in tmpls},
                 "matches": {k: agg[-1][k]["match_embeddings"] for k in tmpls},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roofline, "rooflines": [roof_lcc, roof_search],
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:

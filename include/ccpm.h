@@ -154,6 +154,9 @@ typedef struct {
     int64_t  lcc_active_vertices;  /* active vertices, summed over rounds      */
     int64_t  kernel_launches;      /* all kernels this call launched          */
     int64_t  lcc_compactions;      /* row compactions (K4) between LCC rounds */
+    double   ms_search_kernel;     /* device time of the NLCC search kernels  */
+    int64_t  search_launches;      /* their launches                          */
+    int64_t  search_entries_nlcc;  /* row entries those kernels examined      */
 } ccpm_counts;
 
 /* ---------------------------------------------------------------- context */

@@ -53,7 +53,8 @@ class Counts(ctypes.Structure):
                 ("lcc_launches", ctypes.c_int64), ("ms_lcc_kernel", ctypes.c_double),
                 ("lcc_alg_bytes", ctypes.c_int64), ("lcc_row_entries", ctypes.c_int64),
                 ("lcc_active_vertices", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("lcc_compactions", ctypes.c_int64)]
+                ("lcc_compactions", ctypes.c_int64), ("ms_search_kernel", ctypes.c_double),
+                ("search_launches", ctypes.c_int64), ("search_entries_nlcc", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

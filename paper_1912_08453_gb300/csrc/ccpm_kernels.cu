@@ -1678,7 +1678,8 @@ struct Workspace {
     unsigned long long *hist = nullptr;      // 33 counters (k_omega_hist)
     unsigned long long *hist_h = nullptr;
     DevPlan *plans_h = nullptr;      // pinned staging for plan uploads
-    cudaEvent_t ev[10] = {};
+    unsigned long long *aux_h = nullptr;     // pinned: counters snapshotted in stream order
+    cudaEvent_t ev[12] = {};
     // compacted rows (K4), two generations; allocated at the first compaction
     int64_t *sub_rp[2] = {nullptr, nullptr};
     int32_t *sub_col[2] = {nullptr, nullptr};
@@ -1792,6 +1793,7 @@ void ws_free(Workspace &w) {
     cudaFree(w.hist);
     if (w.hist_h) cudaFreeHost(w.hist_h);
     if (w.plans_h) cudaFreeHost(w.plans_h);
+    if (w.aux_h) cudaFreeHost(w.aux_h);
     for (auto &e : w.ev) if (e) cudaEventDestroy(e);
     for (int i = 0; i < 2; i++) { cudaFree(w.sub_rp[i]); cudaFree(w.sub_col[i]); cudaFree(w.sub_bits[i]); }
     for (int i = 0; i < 2; i++) cudaFree(w.sub_nlab[i]);
@@ -1833,6 +1835,7 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     CU(ctx, cudaMalloc((void **)&w.hist, (kMaxT + 1) * sizeof(unsigned long long)));
     CU(ctx, cudaMallocHost((void **)&w.hist_h, (kMaxT + 1) * sizeof(unsigned long long)));
     CU(ctx, cudaMallocHost((void **)&w.plans_h, kMaxPlans * sizeof(DevPlan)));
+    CU(ctx, cudaMallocHost((void **)&w.aux_h, 4 * sizeof(unsigned long long)));
     CU(ctx, cudaMemsetAsync(w.acc, 0, sizeof(HubAcc) * (size_t)w.acc_cap, ctx->stream));
     for (auto &e : w.ev) CU(ctx, cudaEventCreate(&e));
     return CCPM_OK;
@@ -1952,6 +1955,8 @@ struct Pipeline {
     int64_t windows = 0;
     int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
     double ms_lcc_kernel = 0.0;
+    double ms_search_kernel = 0.0;
+    int64_t search_launches = 0, nlcc_entries = 0;
     int maxc = 0;
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
@@ -2620,12 +2625,16 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, __builtin_popcount(c.vmask), P.launches));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             P.launches++;
+            P.search_launches++;
+            CUF(cudaMemcpyAsync(w.aux_h, &w.st->windows, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CUF(cudaEventRecord(w.ev[10], s));
             if (a.n_items <= w.items_cap) {
                 k_nlcc_items<<<grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16), 128, 0, s>>>(a);
             } else {
                 k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
             }
             CUF(cudaGetLastError());
+            CUF(cudaEventRecord(w.ev[11], s));
             P.launches++;
             k_nlcc_apply<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, c.hmask, w.sat,
                                                                         w.om[0], w.om[1], P.lrp, P.lbits, w.st);
@@ -2633,7 +2642,11 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             RCF(P.read_stats());
             if (w.st_h->overflow) over = true;
             P.windows += (int64_t)w.st_h->windows;
+            P.nlcc_entries += (int64_t)(w.st_h->windows - w.aux_h[0]);
             tokens += (int64_t)w.st_h->tokens;
+            float ms_k = 0.f;
+            CUF(cudaEventElapsedTime(&ms_k, w.ev[10], w.ev[11]));
+            P.ms_search_kernel += ms_k;
         }
         bool changed = n_roots > 0 && w.st_h->changed;
         CUF(cudaEventRecord(w.ev[7], s));
@@ -2884,6 +2897,9 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     cn.lcc_alg_bytes = 24 * P.alive + 4 * P.rows + P.rows / 8 + 4 * P.scanned;
     cn.kernel_launches = P.launches;
     cn.lcc_compactions = P.compactions;
+    cn.ms_search_kernel = P.ms_search_kernel;
+    cn.search_launches = P.search_launches;
+    cn.search_entries_nlcc = P.nlcc_entries;
     int status = CCPM_OK;
     if (over || (opt.run_final && !count_valid)) status = CCPM_EBUDGET;
     cn.status = status;
