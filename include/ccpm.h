@@ -207,12 +207,14 @@ int  ccpm_tmpl_set_order(ccpm_tmpl_t t, int n, const int32_t *order);
 
 /* ------------------------------------------------------------------ prune */
 
-/* Run the whole pipeline (Alg. 1 plus the final search) for template t over
- * graph g.  If *out is NULL a result is created; a non-NULL *out made by an
- * earlier call on the same graph is reused (its buffers are overwritten).
- * Returns CCPM_OK, CCPM_EBUDGET (results still valid as a superset of the
- * exact answer when the final search stopped early: count_valid = 0), or an
- * error. */
+/* Run the whole pipeline (Alg. 1 plus the final search of Remark 1) for
+ * template t over graph g.  If *out is NULL a result is created; a non-NULL
+ * *out made by an earlier call on the same graph is reused (its buffers are
+ * overwritten).  Returns CCPM_OK, CCPM_EBUDGET or an error.  CCPM_EBUDGET
+ * means a budget was reached: past options.max_embeddings the match count is
+ * not reported (count_valid = 0) while omega and the edge bitmap are still
+ * the exact answer; past options.search_budget a search kept its root as
+ * satisfied, so omega and the bitmap are a superset of the exact answer. */
 int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
                 const ccpm_options *opt, ccpm_result_t *out);
 
