@@ -358,7 +358,8 @@ void build_dev_tmpl(const Template &t, DevTmpl &d) {
 }
 
 void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int root,
-                const int64_t *label_freq, bool with_marks, DevPlan &p, int second) {
+                const int64_t *label_freq, bool with_marks, DevPlan &p, int second,
+                const unsigned long long *qlive) {
     std::memset(&p, 0, sizeof(p));
     int pos_of[kMaxT];
     for (int i = 0; i < kMaxT; i++) pos_of[i] = -1;
@@ -375,7 +376,7 @@ void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int roo
             if (!((svert >> q) & 1u) || ((placed >> q) & 1u)) continue;
             int links = popc(sadj[q] & placed);
             if (links == 0) continue;
-            int64_t f = label_freq ? label_freq[t.labels[q]] : 0;
+            int64_t f = qlive ? (int64_t)qlive[q] : (label_freq ? label_freq[t.labels[q]] : 0);
             if (links > best_links || (links == best_links && f < best_freq)) {
                 best = q; best_links = links; best_freq = f;
             }

@@ -79,10 +79,12 @@ int  constraints_generate(Template &t, std::string &err);
 uint64_t count_automorphisms(const Template &t);
 void build_dev_tmpl(const Template &t, DevTmpl &d);
 // order[] of S's vertices from `root`: greedy, most back edges first, then
-// rarest background label, then lowest id.
+// fewest live candidates (qlive[q]: vertices whose omega holds q, when given;
+// otherwise the background frequency of q's label), then lowest id.
 // second >= 0 fixes position 1 (a template neighbour of root): plans rooted at
 // a template edge.
 void build_plan(const Template &t, uint32_t svert, const uint32_t *sadj, int root,
-                const int64_t *label_freq, bool with_marks, DevPlan &p, int second = -1);
+                const int64_t *label_freq, bool with_marks, DevPlan &p, int second = -1,
+                const unsigned long long *qlive = nullptr);
 
 }  // namespace ccpm

@@ -654,6 +654,9 @@ struct CompactArgs {
     const int64_t *sub_rp;        // offsets of the new rows
     int32_t *sub_col;             // the new rows, grouped by label, ids ascending
     uint8_t *sub_nlab;            // inside a group, and their labels
+    int32_t *dslot;               // per live vertex: its slot in gdir
+    int64_t *gdir;                // per slot: start of each label group, then the row end
+    unsigned int *n_slots;        // slot counter (zeroed before)
 };
 
 // Position of the r-th (0-based) set bit of x (x has more than r set bits):
@@ -814,7 +817,17 @@ k_compact_fill(CompactArgs a) {
                 if (c2 < ci.c) before += x;
             }
         }
-        place_ranked(a, beg, end, a.sub_rp[ci.v] + (int64_t)lane_excl(tot) + before);
+        const int64_t gstart = a.sub_rp[ci.v] + (int64_t)lane_excl(tot);
+        if (ci.c == 0) {
+            unsigned int slot = 0;
+            if (lane == 0) {
+                slot = atomicAdd(a.n_slots, 1u);
+                a.dslot[ci.v] = (int32_t)slot;
+            }
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            if (lane <= a.n_rank) a.gdir[(int64_t)slot * (a.n_rank + 1) + lane] = gstart;
+        }
+        place_ranked(a, beg, end, gstart + before);
     }
     // whole rows, 32 list entries per warp step.  A row keeping at most 16
     // entries (most of them, once the first round has run) is written by its
@@ -834,9 +847,13 @@ k_compact_fill(CompactArgs a) {
             out = a.sub_rp[vl];
             k = a.sub_rp[vl + 1] - out;
         }
-        if (vl >= 0 && k > 0 && k <= 16) {
+        if (vl >= 0 && k <= 16) {
             const int64_t stop = out + k;
-            for (int r = 0; r < a.n_rank && out < stop; r++) {
+            const unsigned int slot = atomicAdd(a.n_slots, 1u);
+            a.dslot[vl] = (int32_t)slot;
+            int64_t *dir = a.gdir + (int64_t)slot * (a.n_rank + 1);
+            for (int r = 0; r < a.n_rank; r++) {
+                dir[r] = out;
                 const uint8_t L = a.rank_label[r];
                 for (int64_t wi = beg >> 5; (wi << 5) < end && out < stop; wi++) {
                     uint32_t word = a.bits[wi];
@@ -853,13 +870,23 @@ k_compact_fill(CompactArgs a) {
                     }
                 }
             }
+            dir[a.n_rank] = stop;
         }
         for (uint32_t big = __ballot_sync(FULL_MASK, vl >= 0 && k > 16); big; big &= big - 1u) {
             const int src = __ffs(big) - 1;
             const int64_t rb = __shfl_sync(FULL_MASK, beg, src), re = __shfl_sync(FULL_MASK, end, src);
             const int64_t ro = __shfl_sync(FULL_MASK, out, src);
+            const int32_t rv = __shfl_sync(FULL_MASK, vl, src);
             const uint32_t rc = rank_counts(a, rb, re);
-            place_ranked(a, rb, re, ro + (int64_t)lane_excl(lane < a.n_rank ? rc : 0u));
+            const int64_t gstart = ro + (int64_t)lane_excl(lane < a.n_rank ? rc : 0u);
+            unsigned int slot = 0;
+            if (lane == 0) {
+                slot = atomicAdd(a.n_slots, 1u);
+                a.dslot[rv] = (int32_t)slot;
+            }
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            if (lane <= a.n_rank) a.gdir[(int64_t)slot * (a.n_rank + 1) + lane] = gstart;
+            place_ranked(a, rb, re, gstart);
         }
     }
 }
@@ -936,6 +963,10 @@ struct __align__(16) SearchItem {
 struct SearchArgs {
     const int64_t *rp;
     const int32_t *col;       // id-sorted rows (edge-bitmap indexing)
+    const int32_t *dslot;     // compacted rows: slot of a live vertex in gdir
+    const int64_t *gdir;      // per slot: start of each label group, then the row end
+    int n_rank;               // distinct template labels (groups per compacted row)
+    uint8_t lab_rank[256];    // rank of a template label among them
     const int64_t *rl;        // offsets of the rows the searches scan:
     const int32_t *lcol;      // the full rows grouped by neighbour label, ids ascending
     const uint8_t *nlab;      // inside a group, with nlab = label of lcol[e]; or
@@ -971,27 +1002,27 @@ struct WarpSearch {
     int64_t blo[kMaxT][kMaxBack], bhi[kMaxT][kMaxBack];
 };
 
-// [lo, hi) of the label-L group in the label-grouped row of x; the whole row
-// when the rows are compacted ones (nlab == nullptr: ids ascending, every
-// label mixed; candidates are then told apart by their omega alone).
-__device__ __forceinline__ void label_range(const int64_t *rp, const uint8_t *nlab, int32_t x, uint32_t L,
-                                            int64_t &lo, int64_t &hi) {
-    const int64_t a = rp[x], b = rp[x + 1];
-    if (nlab == nullptr) {
-        lo = a;
-        hi = b;
+// [lo, hi) of the label-L group in the label-grouped row of x: read from the
+// group directory of the compacted rows, else found by binary search in the
+// full rows.
+__device__ __forceinline__ void label_range(const SearchArgs &a, int32_t x, uint32_t L, int64_t &lo, int64_t &hi) {
+    if (a.gdir) {
+        const int64_t *d = a.gdir + (int64_t)__ldg(a.dslot + x) * (a.n_rank + 1) + a.lab_rank[L];
+        lo = __ldg(d);
+        hi = __ldg(d + 1);
         return;
     }
-    int64_t l = a, h = b;
+    const int64_t b0 = a.rl[x], b1 = a.rl[x + 1];
+    int64_t l = b0, h = b1;
     while (l < h) {
         int64_t m = (l + h) >> 1;
-        if ((uint32_t)__ldg(nlab + m) < L) l = m + 1; else h = m;
+        if ((uint32_t)__ldg(a.nlab + m) < L) l = m + 1; else h = m;
     }
     lo = l;
-    h = b;
+    h = b1;
     while (l < h) {
         int64_t m = (l + h) >> 1;
-        if ((uint32_t)__ldg(nlab + m) <= L) l = m + 1; else h = m;
+        if ((uint32_t)__ldg(a.nlab + m) <= L) l = m + 1; else h = m;
     }
     hi = l;
 }
@@ -999,7 +1030,7 @@ __device__ __forceinline__ void label_range(const int64_t *rp, const uint8_t *nl
 // Is u (label L) a neighbour of x?  Binary search inside x's label-L group.
 __device__ __forceinline__ bool adjacent(const SearchArgs &a, int32_t x, int32_t u, uint32_t L) {
     int64_t lo, hi;
-    label_range(a.rl, a.nlab, x, L, lo, hi);
+    label_range(a, x, L, lo, hi);
     const int64_t stop = hi;
     while (lo < hi) {
         int64_t m = (lo + hi) >> 1;
@@ -1031,7 +1062,7 @@ __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P
         uint32_t m = cm;
         for (int i = 0; i < lane; i++) m &= m - 1u;
         j = __ffs(m) - 1;
-        label_range(a.rl, a.nlab, W.psi[j], P.lab[d], lo, hi);
+        label_range(a, W.psi[j], P.lab[d], lo, hi);
         len = hi - lo;
     }
     int best = lane;
@@ -1266,7 +1297,7 @@ k_expand(SearchArgs a) {
             const DevPlan &P = a.plans[a.enum_heads ? 0 : h];
             const int q1 = P.q[1];
             int64_t lo, hi;
-            label_range(a.rl, a.nlab, v, P.lab[1], lo, hi);
+            label_range(a, v, P.lab[1], lo, hi);
             entries += (unsigned long long)(hi - lo);
             for (int64_t base = lo; base < hi; base += 32) {
                 const int64_t e = base + lane;
@@ -1687,6 +1718,10 @@ struct Workspace {
     int64_t sub_cap[2] = {0, 0};     // entries sub_col / sub_bits can hold
     int64_t *deg = nullptr;          // n + 1 kept-entry counts, scanned into sub_rp
     uint8_t *sub_nlab[2] = {nullptr, nullptr};
+    int32_t *sub_dslot[2] = {nullptr, nullptr};   // live vertex -> label-group directory slot
+    int64_t *sub_gdir[2] = {nullptr, nullptr};
+    int64_t gdir_cap[2] = {0, 0};
+    unsigned int *slot_ctr = nullptr;
     uint32_t *piece_cnt = nullptr;   // kept entries per (piece, label rank) of long rows
     int64_t piece_cap = 0;
     void *scan_tmp = nullptr;
@@ -1796,7 +1831,8 @@ void ws_free(Workspace &w) {
     if (w.aux_h) cudaFreeHost(w.aux_h);
     for (auto &e : w.ev) if (e) cudaEventDestroy(e);
     for (int i = 0; i < 2; i++) { cudaFree(w.sub_rp[i]); cudaFree(w.sub_col[i]); cudaFree(w.sub_bits[i]); }
-    for (int i = 0; i < 2; i++) cudaFree(w.sub_nlab[i]);
+    for (int i = 0; i < 2; i++) { cudaFree(w.sub_nlab[i]); cudaFree(w.sub_dslot[i]); cudaFree(w.sub_gdir[i]); }
+    cudaFree(w.slot_ctr);
     cudaFree(w.deg); cudaFree(w.piece_cnt); cudaFree(w.scan_tmp);
     w = Workspace{};
 }
@@ -1966,6 +2002,10 @@ struct Pipeline {
     int compact_mode = 0;           // options.compact
     int64_t compactions = 0;
     const uint8_t *lnlab = nullptr; // labels of lcol (compacted rows are label-grouped)
+    const int32_t *ldslot = nullptr;  // their label-group directory
+    const int64_t *lgdir = nullptr;
+    int lnrank = 0;
+    uint8_t llab_rank[256] = {};
     int64_t last_kept = -1, last_rows = -1;   // the latest round: entries still active, rows of the survivors
 
     // alive counts per template vertex (w.hist_h[0..31]) and total bits ([32])
@@ -2068,6 +2108,15 @@ struct Pipeline {
         return CCPM_OK;
     }
 
+    // Label-group directory of the compacted rows for the searches (none on
+    // the full rows: they find groups by binary search).
+    void directory(SearchArgs &a) const {
+        a.dslot = gen >= 0 ? ldslot : nullptr;
+        a.gdir = gen >= 0 ? lgdir : nullptr;
+        a.n_rank = lnrank;
+        std::memcpy(a.lab_rank, llab_rank, sizeof(llab_rank));
+    }
+
     // Compact when most entries of the live rows are inactive: the next round
     // (or search) would mostly skip them.
     bool want_compact() const {
@@ -2122,6 +2171,17 @@ struct Pipeline {
             w.piece_cap = w.chunk_cap * kMaxT;
         }
         if (!w.sub_rp[nb] && (rc = dalloc(ctx, &w.sub_rp[nb], (size_t)g->n + 1))) return rc;
+        if (!w.sub_dslot[nb] && (rc = dalloc(ctx, &w.sub_dslot[nb], (size_t)g->n))) return rc;
+        if (!w.slot_ctr && (rc = dalloc(ctx, &w.slot_ctr, 1))) return rc;
+        const int64_t dir_need = (n_small + n_med + n_chunk + 1) * (int64_t)(nl + 1);
+        if (dir_need > w.gdir_cap[nb]) {
+            cudaFree(w.sub_gdir[nb]);
+            w.sub_gdir[nb] = nullptr;
+            w.gdir_cap[nb] = 0;
+            const int64_t cap = std::max<int64_t>(dir_need, w.gdir_cap[nb ^ 1]);
+            if ((rc = dalloc(ctx, &w.sub_gdir[nb], (size_t)cap))) return rc;
+            w.gdir_cap[nb] = cap;
+        }
         const int64_t need = last_kept + 64;
         if (need > w.sub_cap[nb]) {
             cudaFree(w.sub_col[nb]);
@@ -2179,6 +2239,10 @@ struct Pipeline {
         ca.sub_rp = w.sub_rp[nb];
         ca.sub_col = w.sub_col[nb];
         ca.sub_nlab = w.sub_nlab[nb];
+        ca.dslot = w.sub_dslot[nb];
+        ca.gdir = w.sub_gdir[nb];
+        ca.n_slots = w.slot_ctr;
+        CU(ctx, cudaMemsetAsync(w.slot_ctr, 0, sizeof(unsigned int), s));
         launches++;
         k_compact_fill<<<grid_for(ctx, n_chunk * 32 + n_med + n_small, 256, 8), 256, 0, s>>>(ca);
         CU(ctx, cudaGetLastError());
@@ -2189,6 +2253,10 @@ struct Pipeline {
         lcol = w.sub_col[nb];
         lnlab = w.sub_nlab[nb];
         lbits = w.sub_bits[nb];
+        ldslot = w.sub_dslot[nb];
+        lgdir = w.sub_gdir[nb];
+        lnrank = nl;
+        std::memcpy(llab_rank, ca.lab_rank, sizeof(llab_rank));
         gen = nb;
         dense = true;
         compactions++;
@@ -2586,7 +2654,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         uint32_t sadj[kMaxT] = {};
         for (auto &e : c.edges) { sadj[e.first] |= 1u << e.second; sadj[e.second] |= 1u << e.first; }
         for (int h = 0; h < kMaxT; h++)
-            if ((c.hmask >> h) & 1u) build_plan(t, c.vmask, sadj, h, g->label_freq, false, w.plans_h[h]);
+            if ((c.hmask >> h) & 1u) build_plan(t, c.vmask, sadj, h, g->label_freq, false, w.plans_h[h], -1, w.hist_h);
         CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * kMaxT, cudaMemcpyHostToDevice, s));
         CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
         P.launches++;
@@ -2604,6 +2672,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.rl = P.gen >= 0 ? P.lrp : g->rp;
             a.lcol = P.gen >= 0 ? P.lcol : g->lcol;
             a.nlab = P.gen >= 0 ? P.lnlab : g->nlab;
+        P.directory(a);
+            P.directory(a);
             a.om = w.om[P.cur];
             a.roots = w.roots;
             a.n_roots = n_roots;
@@ -2708,13 +2778,18 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             CU(ctx, cudaGetLastError());
             return P.read_stats();
         };
+        // the final enumeration keeps the background label frequencies (measured
+        // faster than ordering by live candidates there)
+        const unsigned long long *live = nullptr;
         int root = 0;
-        for (int q = 1; q < t.n0; q++)
-            if (g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]]) root = q;
+        for (int q = 1; q < t.n0; q++) {
+            const bool fewer = live ? live[q] < live[root] : g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]];
+            if (fewer) root = q;
+        }
         // one pass over every match from roots of `root`: count (mode kCount) or
         // count and mark (kMark); returns overflow of the cap
         auto count_pass = [&](int mode, const uint32_t *om_src, uint64_t cap, uint64_t &found, bool &capped) -> int {
-            build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0]);
+            build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0], -1, live);
             CU(ctx, cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan), cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
             P.launches++;
@@ -2777,7 +2852,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             // (A) every (v, q): some match has phi(q) = v?  Found embeddings also
             // satisfy the other (vertex, template vertex) pairs they place and mark
             // their edges.
-            for (int q = 0; q < t.n0; q++) build_plan(t, all, t.adj, q, g->label_freq, true, w.plans_h[q]);
+            for (int q = 0; q < t.n0; q++) build_plan(t, all, t.adj, q, g->label_freq, true, w.plans_h[q], -1, live);
             CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * (size_t)t.n0, cudaMemcpyHostToDevice, s));
             CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
             P.launches++;
@@ -2830,7 +2905,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                 for (int o = 0; o < tab.n; o++) {
                     tab.a[o] = (int8_t)oriented[o0 + (size_t)o].first;
                     tab.b[o] = (int8_t)oriented[o0 + (size_t)o].second;
-                    build_plan(t, all, t.adj, tab.a[o], g->label_freq, true, w.plans_h[o], tab.b[o]);
+                    build_plan(t, all, t.adj, tab.a[o], g->label_freq, true, w.plans_h[o], tab.b[o], live);
                 }
                 CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * (size_t)tab.n, cudaMemcpyHostToDevice, s));
                 CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
