@@ -222,18 +222,29 @@ def batch_templates(cfg):
 
 
 def run_batch_workload(args, cfg):
-    """Plain (one template at a time, fixed order) vs batched + learned order."""
+    """Plain (one template at a time, fixed order) vs batched + learned order.
+    Under torchrun the templates are dealt to the ranks (longest first, by
+    rank 0's warm-up times); each rank prunes its share over its own copy of
+    the graph, and the step time is the maximum over ranks."""
     import torch
     from paper_1912_08453_gb300.build import build
-    build()
-    from paper_1912_08453_gb300 import ccpm, ordering
-    g = make_graph(cfg, device="cuda:0")
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1912_08453_gb300 import ccpm, ordering, sharding
+    g = make_graph(cfg, device=f"cuda:{local}")
     torch.cuda.empty_cache()
     stream = torch.cuda.Stream()
-    ctx = ccpm.Context(0, stream=stream.cuda_stream)
+    ctx = ccpm.Context(local, stream=stream.cuda_stream)
     graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
-    tmpls = batch_templates(cfg)
-    hs = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls]
+    tmpls_all = batch_templates(cfg)
+    hs_all = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls_all]
     cap = ccpm.options(max_embeddings=args.count_cap)
 
     def plain(results):
@@ -252,9 +263,19 @@ def run_batch_workload(args, cfg):
         return out, ev0.elapsed_time(ev1)
 
     with torch.cuda.stream(stream):
-        res_plain = [None] * len(hs)
+        # warm-up over every template; rank 0's times deal the templates
+        res_all = [None] * len(hs_all)
         for _ in range(args.warmup):
-            plain(res_plain)
+            for i, h in enumerate(hs_all):
+                res_all[i] = ccpm.prune(ctx, graph, h, cap, result=res_all[i], allow_budget=True)
+        costs = torch.tensor([r.counts()["ms_total"] for r in res_all], dtype=torch.float64,
+                             device=f"cuda:{local}")
+        if world > 1:
+            torch.distributed.broadcast(costs, 0)
+        mine = sharding.deal(costs.tolist(), world)[rank]
+        hs = [hs_all[i] for i in mine]
+        tmpls = [tmpls_all[i] for i in mine]
+        res_plain = [res_all[i] for i in mine]
         # the plain pipeline's own logs train the ordering network
         recs = [rec for r in res_plain for rec in r.logs()]
         X, y = ordering.targets_from(recs)
@@ -282,15 +303,26 @@ def run_batch_workload(args, cfg):
                for a, b in zip(res_plain, res_batch))
     edges = sum(r.counts()["edges_scanned_lcc"] + r.counts()["edges_scanned_search"] for r in res_batch)
     ms_plain, ms_batch = statistics.median(t_plain), statistics.median(t_batch)
-    line = {"metric": METRIC, "value": edges / (ms_batch / 1e3), "unit": "edges scanned/s", "n_gpus": 1,
+    dev = f"cuda:{local}"
+    ms_plain, _, _ = sharding.reduce_step(ms_plain, 0, True, device=dev)
+    ms_batch, edges, same = sharding.reduce_step(ms_batch, edges, same, device=dev)
+    ms_bfix, _, _ = sharding.reduce_step(statistics.median(t_bfix), 0, True, device=dev)
+    ms_plearn, _, _ = sharding.reduce_step(statistics.median(t_plearn), 0, True, device=dev)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": edges / (ms_batch / 1e3), "unit": "edges scanned/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
             "config": {"workload": args.workload, "graph": f"R-MAT scale {cfg['scale']}, degree labels",
-                       "n": g.n, "m_dir": g.m_dir, "templates": len(hs),
-                       "template_sizes": sorted({t.n0 for t in tmpls}),
+                       "n": g.n, "m_dir": g.m_dir, "templates": len(hs_all), "templates_rank0": len(hs),
+                       "template_sizes": sorted({t.n0 for t in tmpls_all}),
+                       "parallelism": f"templates dealt over {world} ranks" if world > 1 else "one GPU",
                        "l2": "inputs larger than L2 (the 513 MB column array)"},
             "plain_ms": ms_plain, "batched_learned_ms": ms_batch, "speedup": ms_plain / ms_batch,
-            "batched_fixed_ms": statistics.median(t_bfix), "plain_learned_ms": statistics.median(t_plearn),
+            "batched_fixed_ms": ms_bfix, "plain_learned_ms": ms_plearn,
             "plain_split_ms": {k: sum(r.counts()[k] for r in res_plain) for k in ("ms_lcc", "ms_nlcc", "ms_final")},
             "count_cap": args.count_cap,
             "counts_valid": int(sum(r.counts()["count_valid"] for r in res_plain)),
@@ -363,13 +395,8 @@ def main():
         clk = clocks.stop()
     edges = sum(c["edges_scanned_lcc"] + c["edges_scanned_search"] for st in agg for c in st.values())
     total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
-        e = torch.tensor([edges], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        total_ms, edges = float(t.item()), float(e.item())
+    from paper_1912_08453_gb300 import sharding
+    total_ms, edges, _ = sharding.reduce_step(total_ms, edges, True, device=f"cuda:{local}")
     value = edges / (total_ms / 1e3)
     tts = {k: statistics.mean(st[k]["ms_total"] for st in agg) for k in tmpls}
 
