@@ -56,7 +56,7 @@ struct RoundStats {
     unsigned int n_roots;
     unsigned int n_items;         // (root, head, first candidate) search items
     unsigned int overflow;        // a search hit its budget
-    unsigned int pad;
+    unsigned int n_spill;         // items handed on by searches that ran long
 };
 
 struct HubAcc {                   // partial LCC state of one split row
@@ -792,16 +792,15 @@ k_compact_count(CompactArgs a) {
     }
 }
 
-// Write the new rows.  Pieces of long rows: rank r's group starts after the
-// lower ranks of the whole row, and a piece's entries of rank r follow those
-// of the row's earlier pieces.  Whole rows: one pass when the row keeps at
-// most 32 entries (a warp-wide stable sort by rank), else count then place.
+// Write the new rows and their label-group directory.  Pieces of long rows:
+// rank r's group starts after the lower ranks of the whole row, and a piece's
+// entries of rank r follow those of the row's earlier pieces.  Whole rows:
+// by one lane when the row keeps at most 16 entries, else by the warp.
 __global__ void __launch_bounds__(256)
 k_compact_fill(CompactArgs a) {
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = (int)lane_id();
-    const uint32_t below = (1u << lane) - 1u;
     for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
         const ChunkItem ci = a.chunk_in[it];
         if (__ldg(a.om + ci.v) == 0u) continue;
@@ -986,6 +985,9 @@ struct SearchArgs {
     SearchItem *items;        // split search work: partial embeddings
     int64_t n_items;
     int64_t items_cap;
+    SearchItem *spill;        // a search that has scanned spill_after windows hands its
+    int64_t spill_cap;        // untried candidates on here as new items (0: never)
+    uint64_t spill_after;
     int enum_heads;           // k_expand: 1 = final search (one head), 0 = NLCC
 };
 
@@ -1000,6 +1002,9 @@ struct WarpSearch {
     uint32_t chk[kMaxT];      // further joins, looked up from scratch per candidate
     int nb[kMaxT];            // joins with a stored label group
     int64_t blo[kMaxT][kMaxBack], bhi[kMaxT][kMaxBack];
+    const uint32_t *done_word;  // existence: the answer is known once this bit is set
+    uint32_t done_bit;          // (by another warp's embedding); nullptr: never
+    int head;                   // plan slot of the running item (spilled items keep it)
 };
 
 // [lo, hi) of the label-L group in the label-grouped row of x: read from the
@@ -1153,6 +1158,67 @@ __device__ __forceinline__ void mark_vertices(const SearchArgs &a, const DevPlan
 // and mark the vertices and edges of every one.
 constexpr int kExist = 0, kCount = 1, kMark = 2;
 
+// Hand the rest of a long search to other warps: for every open level L
+// (d0..d) each untried candidate c -- the remaining bits of the level's
+// tested window and every valid entry of its untested range -- becomes an item
+// (psi[0..L-1], c) of depth L+1 in the spill list; for counting, candidates
+// of the last position are counted here instead.  The items are counted
+// first and written only if they all fit.  Returns false (the search goes on
+// where it is) when they do not.
+template <int MODE>
+__device__ bool spill(const SearchArgs &a, const DevPlan &P, WarpSearch &W, int d0, int d,
+                      unsigned long long &matches) {
+    const int lane = (int)lane_id();
+    const uint32_t below = (1u << lane) - 1u;
+    const int k = P.k;
+    unsigned long long total = 0, direct = 0;
+    for (int L = d0; L <= d; L++) {
+        unsigned long long cnt = (unsigned long long)__popc(W.mask[L]);
+        for (int64_t pos = W.pos[L]; pos < W.end[L]; pos += 32) {
+            int32_t u;
+            const bool ok = test_candidate(a, P, W, L, pos + lane, W.end[L], u);
+            cnt += (unsigned long long)__popc(__ballot_sync(FULL_MASK, ok));
+        }
+        if (MODE == kCount && L == k - 1) direct += cnt; else total += cnt;
+    }
+    unsigned long long base = 0;
+    unsigned int fits = 1;
+    if (lane == 0 && total) {
+        base = atomicAdd(&a.st->n_spill, (unsigned int)total);
+        if (base + total > (unsigned long long)a.spill_cap) {
+            atomicSub(&a.st->n_spill, (unsigned int)total);
+            fits = 0;
+        }
+    }
+    if (!__shfl_sync(FULL_MASK, fits, 0)) return false;
+    base = __shfl_sync(FULL_MASK, base, 0);
+    for (int L = d0; L <= d; L++) {
+        if (MODE == kCount && L == k - 1) continue;
+        SearchItem si;
+        for (int j = 0; j < kItemMaxDepth; j++) si.psi[j] = j < L ? W.psi[j] : 0;
+        si.hd = W.head | ((L + 1) << 8);
+        const uint32_t m = W.mask[L];
+        if ((m >> lane) & 1u) {
+            si.psi[L] = __ldg(a.lcol + W.wbase[L] + lane);
+            a.spill[base + __popc(m & below)] = si;
+        }
+        base += (unsigned long long)__popc(m);
+        for (int64_t pos = W.pos[L]; pos < W.end[L]; pos += 32) {
+            int32_t u;
+            const bool ok = test_candidate(a, P, W, L, pos + lane, W.end[L], u);
+            const uint32_t vm = __ballot_sync(FULL_MASK, ok);
+            if (ok) {
+                si.psi[L] = u;
+                a.spill[base + __popc(vm & below)] = si;
+            }
+            base += (unsigned long long)__popc(vm);
+        }
+    }
+    matches += direct;
+    __syncwarp();
+    return true;
+}
+
 // Depth-first search from positions 0..d0-1 already placed in W.psi.
 template <int MODE>
 __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpSearch &W,
@@ -1174,6 +1240,24 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
             const int64_t pos = W.pos[d], end = W.end[d];
             if (pos >= end) { d--; continue; }
             if (++used > a.budget) { over = true; return MODE == kExist; }
+            if ((used & 31u) == 0u && MODE != kMark) {
+                // every 32 windows: has another warp answered this existence
+                // question already, or has the count run past its cap?
+                unsigned int stop = 0;
+                if (lane == 0) {
+                    if (MODE == kExist)
+                        stop = W.done_word && (*(volatile const uint32_t *)W.done_word & W.done_bit);
+                    else
+                        stop = matches > a.cap || *(volatile const unsigned int *)&a.st->overflow;
+                }
+                if (__shfl_sync(FULL_MASK, stop, 0)) {
+                    if (MODE == kCount) over = true;
+                    return false;
+                }
+            }
+            if (a.spill_after && used > a.spill_after && d < kItemMaxDepth &&
+                spill<MODE>(a, P, W, d0, d, matches))
+                return false;                       // the rest runs as new items
             entries += (unsigned long long)min((int64_t)32, end - pos);
             int32_t u;
             const bool ok = test_candidate(a, P, W, d, pos + lane, end, u);
@@ -1225,7 +1309,7 @@ k_nlcc_search(SearchArgs a) {
         uint32_t sat = 0;
         for (uint32_t hm = hv; hm; hm &= hm - 1u) {
             const int h = __ffs(hm) - 1;
-            if (lane == 0) W.psi[0] = v;
+            if (lane == 0) { W.psi[0] = v; W.done_word = nullptr; }
             __syncwarp();
             if (search_from<kExist>(a, a.plans[h], 1, W, entries, matches, over)) sat |= 1u << h;
             __syncwarp();
@@ -1254,7 +1338,7 @@ k_final_search(SearchArgs a) {
         if (__shfl_sync(FULL_MASK, stop, 0)) break;
         const int32_t v = a.roots[it];
         unsigned long long before = matches;
-        if (lane == 0) W.psi[0] = v;
+        if (lane == 0) { W.psi[0] = v; W.done_word = nullptr; }
         __syncwarp();
         search_from<MODE>(a, a.plans[0], 1, W, entries, matches, over);
         __syncwarp();
@@ -1396,6 +1480,7 @@ k_nlcc_items(SearchArgs a) {
             if (lane == 0) done = *(volatile uint32_t *)&a.sat[item.psi[0]] & bit;
             if (__shfl_sync(FULL_MASK, done, 0)) continue;
             if (lane < depth) W.psi[lane] = item.psi[lane];
+            if (lane == 0) { W.done_word = &a.sat[item.psi[0]]; W.done_bit = bit; W.head = h; }
             __syncwarp();
             bool ran_out = false;
             if (search_from<kExist>(a, a.plans[h], depth, W, entries, matches, ran_out)) {
@@ -1441,6 +1526,7 @@ k_final_items(SearchArgs a) {
             const SearchItem item = a.items[it];
             const int depth = item.hd >> 8;
             if (lane < depth) W.psi[lane] = item.psi[lane];
+            if (lane == 0) { W.done_word = nullptr; W.head = item.hd & 0xff; }
             __syncwarp();
             search_from<MODE>(a, a.plans[0], depth, W, entries, matches, over);
             __syncwarp();
@@ -1525,6 +1611,7 @@ k_edge_search(SearchArgs a) {
             if (lane == 0) done = (*(volatile uint32_t *)&a.eb_out[e >> 5] >> (uint32_t)(e & 31)) & 1u;
             if (__shfl_sync(FULL_MASK, done, 0)) continue;
             if (lane < 2) W.psi[lane] = item.psi[lane];
+            if (lane == 0) { W.done_word = &a.eb_out[e >> 5]; W.done_bit = 1u << (uint32_t)(e & 31); }
             __syncwarp();
             const DevPlan &P = a.plans[o];
             bool ran_out = false;
@@ -1700,6 +1787,8 @@ struct Workspace {
     SearchItem *items = nullptr;     // split search work
     int64_t items_cap = 0;
     SearchItem *items2 = nullptr;    // input of a further expansion
+    SearchItem *spill_items = nullptr;   // items handed on by long searches
+    int64_t spill_cap = 0;
     DevPlan *plans = nullptr;
     RoundStats *st = nullptr;        // device
     unsigned long long *next_root = nullptr;   // dynamic root counter of the searches
@@ -1822,7 +1911,7 @@ void ws_free(Workspace &w) {
     cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.ebits);
     cudaFree(w.small[0]); cudaFree(w.small[1]); cudaFree(w.med[0]); cudaFree(w.med[1]);
     cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
-    cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
+    cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.spill_items); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
     if (w.st_h) cudaFreeHost(w.st_h);
     if (w.cnt_h) cudaFreeHost(w.cnt_h);
     cudaFree(w.hist);
@@ -1862,6 +1951,8 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     w.items_cap = std::min<int64_t>(std::max<int64_t>(g->m, (int64_t)1 << 22), (int64_t)1 << 24);
     if ((rc = dalloc(ctx, &w.items, (size_t)w.items_cap))) return rc;
     if ((rc = dalloc(ctx, &w.items2, (size_t)kExpandBelow))) return rc;
+    w.spill_cap = std::max<int64_t>(w.items_cap / 4, (int64_t)1 << 20);
+    if ((rc = dalloc(ctx, &w.spill_items, (size_t)w.spill_cap))) return rc;
     if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxPlans))) return rc;
     if ((rc = dalloc(ctx, &w.st, 1))) return rc;
     if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
@@ -1948,6 +2039,48 @@ int grid_for(ccpm_ctx *ctx, int64_t work_items, int per_block, int blocks_per_sm
     return (int)std::min(need, cap);
 }
 
+// Windows a search scans before it hands the rest of its work to other warps.
+constexpr uint64_t kSpillAfter = 2048;
+
+// Run an item kernel, then again over the items long searches handed on, until
+// none are left (each round of items is strictly deeper, so at most one pass
+// per template position).  kind 0: NLCC existence (k_nlcc_items), 1: final
+// count, 2: final count and mark.  Counting stops once the cap is passed.
+int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, int64_t &launches, int64_t &passes) {
+    cudaStream_t s = ctx->stream;
+    SearchItem *bufs[2] = {w.items, w.spill_items};
+    const int64_t caps[2] = {w.items_cap, w.spill_cap};
+    int cur = 0;
+    for (;;) {
+        a.items = bufs[cur];
+        a.spill = bufs[cur ^ 1];
+        a.spill_cap = caps[cur ^ 1];
+        a.spill_after = kSpillAfter;
+        CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+        CU(ctx, cudaMemsetAsync(&w.st->n_spill, 0, sizeof(unsigned int), s));
+        const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
+        launches++;
+        passes++;
+        if (kind == 0) k_nlcc_items<<<gi, 128, 0, s>>>(a);
+        else if (kind == 1) k_final_items<kCount><<<gi, 128, 0, s>>>(a);
+        else k_final_items<kMark><<<gi, 128, 0, s>>>(a);
+        CU(ctx, cudaGetLastError());
+        CU(ctx, cudaMemcpyAsync(&w.aux_h[1], &w.st->n_spill, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaMemcpyAsync(&w.aux_h[2], &w.st->overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        const unsigned int spilled = (unsigned int)(w.aux_h[1] & 0xFFFFFFFFull);
+        const unsigned int over = (unsigned int)(w.aux_h[2] & 0xFFFFFFFFull);
+        if (spilled == 0 || (kind == 1 && over)) break;
+        a.n_items = spilled;
+        cur ^= 1;
+    }
+    a.items = w.items;
+    a.spill = nullptr;
+    a.spill_after = 0;
+    return CCPM_OK;
+}
+
+
 // Ordering features of one constraint in the current state (alive[q] =
 // vertices with q in omega, total = sum of |omega|), step = constraints run.
 void constraint_features(const Template &t, const HostConstraint &c, const unsigned long long *alive,
@@ -1992,7 +2125,7 @@ struct Pipeline {
     int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
     double ms_lcc_kernel = 0.0;
     double ms_search_kernel = 0.0;
-    int64_t search_launches = 0, nlcc_entries = 0;
+    int64_t search_launches = 0, nlcc_entries = 0, item_passes = 0;
     int maxc = 0;
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
@@ -2672,7 +2805,6 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.rl = P.gen >= 0 ? P.lrp : g->rp;
             a.lcol = P.gen >= 0 ? P.lcol : g->lcol;
             a.nlab = P.gen >= 0 ? P.lnlab : g->nlab;
-        P.directory(a);
             P.directory(a);
             a.om = w.om[P.cur];
             a.roots = w.roots;
@@ -2694,13 +2826,13 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.n_items = w.st_h->n_items;
             if (a.n_items <= w.items_cap) RCF(expand_more(ctx, w, a, __builtin_popcount(c.vmask), P.launches));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
-            P.launches++;
             P.search_launches++;
             CUF(cudaMemcpyAsync(w.aux_h, &w.st->windows, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CUF(cudaEventRecord(w.ev[10], s));
             if (a.n_items <= w.items_cap) {
-                k_nlcc_items<<<grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16), 128, 0, s>>>(a);
+                RCF(item_passes(ctx, w, a, 0, P.launches, P.item_passes));
             } else {
+                P.launches++;
                 k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
             }
             CUF(cudaGetLastError());
@@ -2760,6 +2892,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         a.rl = P.gen >= 0 ? P.lrp : g->rp;
         a.lcol = P.gen >= 0 ? P.lcol : g->lcol;
         a.nlab = P.gen >= 0 ? P.lnlab : g->nlab;
+        P.directory(a);
         a.roots = w.roots;
         a.next_root = w.next_root;
         a.plans = w.plans;
@@ -2770,11 +2903,15 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         a.items = w.items;
         a.items_cap = w.items_cap;
         auto run_items = [&](bool edge_pass) -> int {
+            if (!edge_pass) {
+                int rc2 = item_passes(ctx, w, a, 0, P.launches, P.item_passes);
+                return rc2 ? rc2 : P.read_stats();
+            }
+            // edge items keep the entry index in their last two slots: not split further
             CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             P.launches++;
             const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
-            if (edge_pass) k_edge_search<<<gi, 128, 0, s>>>(a);
-            else k_nlcc_items<<<gi, 128, 0, s>>>(a);
+            k_edge_search<<<gi, 128, 0, s>>>(a);
             CU(ctx, cudaGetLastError());
             return P.read_stats();
         };
@@ -2815,16 +2952,16 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             a.n_items = w.st_h->n_items;
             if (a.n_items <= w.items_cap && (rc2 = expand_more(ctx, w, a, t.n0, P.launches))) return rc2;
             CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
-            P.launches++;
             const bool use_items = a.n_items <= w.items_cap;
-            const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
             const int gr = grid_for(ctx, nr * 32, 128, 16);
-            if (mode == kMark) {
-                if (use_items) k_final_items<kMark><<<gi, 128, 0, s>>>(a);
-                else k_final_search<kMark><<<gr, 128, 0, s>>>(a);
+            if (use_items) {
+                if ((rc2 = item_passes(ctx, w, a, mode == kMark ? 2 : 1, P.launches, P.item_passes))) return rc2;
+            } else if (mode == kMark) {
+                P.launches++;
+                k_final_search<kMark><<<gr, 128, 0, s>>>(a);
             } else {
-                if (use_items) k_final_items<kCount><<<gi, 128, 0, s>>>(a);
-                else k_final_search<kCount><<<gr, 128, 0, s>>>(a);
+                P.launches++;
+                k_final_search<kCount><<<gr, 128, 0, s>>>(a);
             }
             CU(ctx, cudaGetLastError());
             if ((rc2 = P.read_stats())) return rc2;
