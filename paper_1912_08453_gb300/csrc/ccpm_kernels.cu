@@ -1005,7 +1005,13 @@ struct WarpSearch {
     const uint32_t *done_word;  // existence: the answer is known once this bit is set
     uint32_t done_bit;          // (by another warp's embedding); nullptr: never
     int head;                   // plan slot of the running item (spilled items keep it)
+    // the first kJoinCache stored join groups of one level, copied to shared
+    // memory when they are short: join tests at that level search them there
+    int jc_level;
+    int jc_len[2];
+    int32_t jc[2][128];
 };
+constexpr int kJoinCache = 2, kJoinCacheLen = 128;
 
 // [lo, hi) of the label-L group in the label-grouped row of x: read from the
 // group directory of the compacted rows, else found by binary search in the
@@ -1059,6 +1065,8 @@ __device__ __forceinline__ int64_t find_entry(const int64_t *rp, const int32_t *
 // label group is shortest; scan that group, look the others up.
 __device__ __forceinline__ void open_level(const SearchArgs &a, const DevPlan &P, WarpSearch &W, int d) {
     const int lane = (int)lane_id();
+    // level d gets new groups: a join cache of this or a deeper level is stale
+    if (lane == 0 && W.jc_level >= d) W.jc_level = -1;
     const uint32_t cm = P.nbr[d];
     const int cnt = __popc(cm);
     int64_t lo = 0, hi = 0, len = INT64_MAX;
@@ -1121,8 +1129,25 @@ __device__ __forceinline__ void mark_edges(const SearchArgs &a, const DevPlan &P
 // Is the entry e of the scanned label group a valid image u for position d?
 // Its omega must hold q_d, it must differ from earlier same-label images, and
 // it must be joined to every other placed neighbour of position d.
-__device__ __forceinline__ bool test_candidate(const SearchArgs &a, const DevPlan &P, const WarpSearch &W,
+// Warp-uniform: make the join cache hold level d's first stored groups.
+__device__ __forceinline__ void join_cache(const SearchArgs &a, WarpSearch &W, int d) {
+    if (W.jc_level == d) return;
+    const int lane = (int)lane_id();
+    const int nb = min(W.nb[d], kJoinCache);
+    for (int b = 0; b < kJoinCache; b++) {
+        const int64_t lo = W.blo[d][b], len = W.bhi[d][b] - lo;
+        const bool fits = b < nb && len <= kJoinCacheLen;
+        if (fits)
+            for (int i = lane; i < (int)len; i += 32) W.jc[b][i] = __ldg(a.lcol + lo + i);
+        if (lane == 0) W.jc_len[b] = fits ? (int)len : -1;
+    }
+    if (lane == 0) W.jc_level = d;
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool test_candidate(const SearchArgs &a, const DevPlan &P, WarpSearch &W,
                                                int d, int64_t e, int64_t end, int32_t &u) {
+    if (W.nb[d] > 0) join_cache(a, W, d);
     u = -1;
     if (e >= end) return false;
     u = __ldg(a.lcol + e);
@@ -1130,6 +1155,16 @@ __device__ __forceinline__ bool test_candidate(const SearchArgs &a, const DevPla
     for (uint32_t sm = P.same[d]; sm; sm &= sm - 1u)
         if (W.psi[__ffs(sm) - 1] == u) return false;
     for (int b = 0; b < W.nb[d]; b++) {
+        if (b < kJoinCache && W.jc_len[b] >= 0) {
+            int lo = 0, hi = W.jc_len[b];
+            const int stop = hi;
+            while (lo < hi) {
+                const int m2 = (lo + hi) >> 1;
+                if (W.jc[b][m2] < u) lo = m2 + 1; else hi = m2;
+            }
+            if (!(lo < stop && W.jc[b][lo] == u)) return false;
+            continue;
+        }
         int64_t lo = W.blo[d][b], hi = W.bhi[d][b];
         const int64_t stop = hi;
         while (lo < hi) {
