@@ -808,13 +808,19 @@ k_compact_fill(CompactArgs a) {
         const int64_t beg = rbeg + (int64_t)ci.c * a.hub_deg;
         const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
         const int64_t p0 = (int64_t)a.acc[ci.slot].pbase;
+        // per rank, the row's total and the part in pieces before this one
+        // (lanes stride over the pieces; lane r keeps rank r's sums)
         uint32_t tot = 0, before = 0;
-        if (lane < a.n_rank) {
-            for (int c2 = 0; c2 < ci.nchunks; c2++) {
-                const uint32_t x = a.piece_cnt[(p0 + c2) * a.n_rank + lane];
-                tot += x;
-                if (c2 < ci.c) before += x;
+        for (int r = 0; r < a.n_rank; r++) {
+            uint32_t t = 0, b = 0;
+            for (int c2 = lane; c2 < ci.nchunks; c2 += 32) {
+                const uint32_t x = a.piece_cnt[(p0 + c2) * a.n_rank + r];
+                t += x;
+                if (c2 < ci.c) b += x;
             }
+            t = __reduce_add_sync(FULL_MASK, t);
+            b = __reduce_add_sync(FULL_MASK, b);
+            if (lane == r) { tot = t; before = b; }
         }
         const int64_t gstart = a.sub_rp[ci.v] + (int64_t)lane_excl(tot);
         if (ci.c == 0) {
@@ -846,26 +852,49 @@ k_compact_fill(CompactArgs a) {
             out = a.sub_rp[vl];
             k = a.sub_rp[vl + 1] - out;
         }
+        // one directory slot per live row, one atomic per warp step
+        const uint32_t live = __ballot_sync(FULL_MASK, vl >= 0);
+        unsigned int slot0 = 0;
+        if (lane == 0 && live) slot0 = atomicAdd(a.n_slots, (unsigned int)__popc(live));
+        const unsigned int slot = __shfl_sync(FULL_MASK, slot0, 0) + (unsigned int)__popc(live & ((1u << lane) - 1u));
+        if (vl >= 0) a.dslot[vl] = (int32_t)slot;
         if (vl >= 0 && k <= 16) {
             const int64_t stop = out + k;
-            const unsigned int slot = atomicAdd(a.n_slots, 1u);
-            a.dslot[vl] = (int32_t)slot;
             int64_t *dir = a.gdir + (int64_t)slot * (a.n_rank + 1);
+            // the row's kept entries (at most 16): positions from the bit words
+            // (four words per step), then their columns, then their labels, each
+            // as independent loads; then placed label by label
+            int32_t eu[16];
+            uint8_t er[16];
+            int n = 0;
+            for (int64_t wi = beg >> 5; (wi << 5) < end && n < 16; wi += 4) {
+                uint32_t wd[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) wd[j] = ((wi + j) << 5) < end ? a.bits[wi + j] : 0u;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    uint32_t word = wd[j];
+                    const int64_t e0 = (wi + j) << 5;
+                    if (e0 < beg) word &= ~0u << (uint32_t)(beg - e0);
+                    if (end - e0 < 32) word &= end > e0 ? (1u << (uint32_t)(end - e0)) - 1u : 0u;
+                    for (; word && n < 16; word &= word - 1u) eu[n++] = (int32_t)(e0 + __ffs(word) - 1 - beg);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                if (i < n) eu[i] = __ldg(a.col + beg + eu[i]);
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                er[i] = i < n ? a.lab_rank[__ldg(a.lab + eu[i])] : (uint8_t)0xFF;
             for (int r = 0; r < a.n_rank; r++) {
                 dir[r] = out;
                 const uint8_t L = a.rank_label[r];
-                for (int64_t wi = beg >> 5; (wi << 5) < end && out < stop; wi++) {
-                    uint32_t word = a.bits[wi];
-                    const int64_t e0 = wi << 5;
-                    if (e0 < beg) word &= ~0u << (uint32_t)(beg - e0);
-                    if (end - e0 < 32) word &= (1u << (uint32_t)(end - e0)) - 1u;
-                    for (; word; word &= word - 1u) {
-                        const int32_t u = __ldg(a.col + e0 + __ffs(word) - 1);
-                        if (__ldg(a.lab + u) == L && out < stop) {
-                            a.sub_col[out] = u;
-                            a.sub_nlab[out] = L;
-                            out++;
-                        }
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    if (er[i] == r && out < stop) {
+                        a.sub_col[out] = eu[i];
+                        a.sub_nlab[out] = L;
+                        out++;
                     }
                 }
             }
@@ -875,16 +904,10 @@ k_compact_fill(CompactArgs a) {
             const int src = __ffs(big) - 1;
             const int64_t rb = __shfl_sync(FULL_MASK, beg, src), re = __shfl_sync(FULL_MASK, end, src);
             const int64_t ro = __shfl_sync(FULL_MASK, out, src);
-            const int32_t rv = __shfl_sync(FULL_MASK, vl, src);
+            const unsigned int rslot = __shfl_sync(FULL_MASK, slot, src);
             const uint32_t rc = rank_counts(a, rb, re);
             const int64_t gstart = ro + (int64_t)lane_excl(lane < a.n_rank ? rc : 0u);
-            unsigned int slot = 0;
-            if (lane == 0) {
-                slot = atomicAdd(a.n_slots, 1u);
-                a.dslot[rv] = (int32_t)slot;
-            }
-            slot = __shfl_sync(FULL_MASK, slot, 0);
-            if (lane <= a.n_rank) a.gdir[(int64_t)slot * (a.n_rank + 1) + lane] = gstart;
+            if (lane <= a.n_rank) a.gdir[(int64_t)rslot * (a.n_rank + 1) + lane] = gstart;
             place_ranked(a, rb, re, gstart);
         }
     }
