@@ -424,7 +424,7 @@ __device__ __forceinline__ uint32_t nbr_mask(uint32_t wv, const SmemTmpl &s) {
 }
 
 template <int MAXC, bool DENSE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_lcc_round(LccArgs a, DevTmpl t) {
     __shared__ SmemTmpl s;
     __shared__ int32_t sbuf[2][8][32];
@@ -645,7 +645,7 @@ struct CompactArgs {
     const int32_t *med_in;
     const ChunkItem *chunk_in;
     const HubAcc *acc;            // first-piece index of each long row (pbase)
-    int64_t n_small, n_med, n_chunk;
+    const RoundStats *lists;      // sizes of the three lists (written by the rebuild before)
     int hub_deg;
     int n_rank;                   // distinct labels of the template
     uint8_t lab_rank[256];        // rank of a template label among them
@@ -780,7 +780,8 @@ k_compact_count(CompactArgs a) {
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = (int)lane_id();
-    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+    const int64_t n_chunk = a.lists->n_chunk;
+    for (int64_t it = gwarp; it < n_chunk; it += nwarps) {
         const ChunkItem ci = a.chunk_in[it];
         if (__ldg(a.om + ci.v) == 0u) continue;
         const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
@@ -801,7 +802,8 @@ k_compact_fill(CompactArgs a) {
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = (int)lane_id();
-    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+    const int64_t n_chunk = a.lists->n_chunk, n_med = a.lists->n_med, n_small = a.lists->n_small;
+    for (int64_t it = gwarp; it < n_chunk; it += nwarps) {
         const ChunkItem ci = a.chunk_in[it];
         if (__ldg(a.om + ci.v) == 0u) continue;
         const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
@@ -837,13 +839,13 @@ k_compact_fill(CompactArgs a) {
     // whole rows, 32 list entries per warp step.  A row keeping at most 16
     // entries (most of them, once the first round has run) is written by its
     // own lane, one pass per label rank; the others by the whole warp in turn.
-    const int64_t n_rows = a.n_med + a.n_small;
+    const int64_t n_rows = n_med + n_small;
     for (int64_t b = gwarp * 32; b < n_rows; b += nwarps * 32) {
         const int64_t idx = b + lane;
         int32_t vl = -1;
         int64_t beg = 0, end = 0, out = 0, k = 0;
         if (idx < n_rows) {
-            vl = idx < a.n_med ? a.med_in[idx] : a.small_in[idx - a.n_med];
+            vl = idx < n_med ? a.med_in[idx] : a.small_in[idx - n_med];
             if (__ldg(a.om + vl) == 0u) vl = -1;
         }
         if (vl >= 0) {
@@ -1298,7 +1300,7 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
             const int64_t pos = W.pos[d], end = W.end[d];
             if (pos >= end) { d--; continue; }
             if (++used > a.budget) { over = true; return MODE == kExist; }
-            if ((used & 31u) == 0u && MODE != kMark) {
+            if ((used & 31u) == 0u) {
                 // every 32 windows: has another warp answered this existence
                 // question already, or has the count run past its cap?
                 unsigned int stop = 0;
@@ -2103,7 +2105,8 @@ constexpr uint64_t kSpillAfter = 2048;
 // Run an item kernel, then again over the items long searches handed on, until
 // none are left (each round of items is strictly deeper, so at most one pass
 // per template position).  kind 0: NLCC existence (k_nlcc_items), 1: final
-// count, 2: final count and mark.  Counting stops once the cap is passed.
+// count, 2: final count and mark.  Counting (and marking) stops once the cap
+// is passed.
 int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, int64_t &launches, int64_t &passes) {
     cudaStream_t s = ctx->stream;
     SearchItem *bufs[2] = {w.items, w.spill_items};
@@ -2128,7 +2131,7 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, int64_t &l
         CU(ctx, cudaStreamSynchronize(s));
         const unsigned int spilled = (unsigned int)(w.aux_h[1] & 0xFFFFFFFFull);
         const unsigned int over = (unsigned int)(w.aux_h[2] & 0xFFFFFFFFull);
-        if (spilled == 0 || (kind == 1 && over)) break;
+        if (spilled == 0 || (kind != 0 && over)) break;
         a.n_items = spilled;
         cur ^= 1;
     }
@@ -2191,6 +2194,7 @@ struct Pipeline {
     uint32_t *lbits = nullptr;
     int gen = -1;                   // compacted generation in use, -1 = full rows
     int compact_mode = 0;           // options.compact
+    int searches_ahead = 0;         // non-local constraints not yet checked
     int64_t compactions = 0;
     const uint8_t *lnlab = nullptr; // labels of lcol (compacted rows are label-grouped)
     const int32_t *ldslot = nullptr;  // their label-group directory
@@ -2310,15 +2314,18 @@ struct Pipeline {
 
     // Compact when most entries of the live rows are inactive: the next round
     // (or search) would mostly skip them.
+    // Automatic mode compacts only while non-local constraints are still to
+    // run: their searches gain the most, while the LCC rounds alone barely pay
+    // for the copy (measured on the scale-22 tree template).
     bool want_compact() const {
         if (compact_mode < 0 || last_rows <= 0) return false;
         if (compact_mode > 0) return last_kept < last_rows;
-        return last_rows >= ((int64_t)1 << 21) && last_kept * 8 < last_rows;
+        return searches_ahead > 0 && last_rows >= ((int64_t)1 << 21) && last_kept * 8 < last_rows;
     }
 
     // Frontier of the live vertices over rows rp (the pieces of a long row
     // consecutive and in order); also makes both omega buffers equal.
-    int rebucket(const int64_t *rp) {
+    int rebucket(const int64_t *rp, bool sync = true) {
         Workspace &w = ctx->ws;
         LabelMask all;
         std::memset(&all, 0xFF, sizeof(all));
@@ -2328,6 +2335,7 @@ struct Pipeline {
                                                                      w.om[cur ^ 1], w.small[li], w.med[li],
                                                                      w.chunk[li], w.acc, w.st, w.hub_deg);
         CU(ctx, cudaGetLastError());
+        if (!sync) return CCPM_OK;
         int rc = read_stats();
         if (rc) return rc;
         n_small = w.st_h->n_small;
@@ -2388,6 +2396,11 @@ struct Pipeline {
             if ((rc = dalloc(ctx, &w.sub_bits[nb], (size_t)(cap / 32 + 2)))) return rc;
             w.sub_cap[nb] = cap;
         }
+        // the lists name every vertex live at the start of the last round; the
+        // rows to copy are those of the vertices live now: list only those (the
+        // kernels read the new sizes on the device, no host sync)
+        const int64_t listed = n_small + n_med + n_chunk;
+        if ((rc = rebucket(lrp, false))) return rc;
         CompactArgs ca{};
         ca.rp = lrp;
         ca.col = lcol;
@@ -2398,9 +2411,7 @@ struct Pipeline {
         ca.med_in = w.med[li];
         ca.chunk_in = w.chunk[li];
         ca.acc = w.acc;
-        ca.n_small = n_small;
-        ca.n_med = n_med;
-        ca.n_chunk = n_chunk;
+        ca.lists = w.st;
         ca.hub_deg = w.hub_deg;
         ca.n_rank = nl;
         std::memset(ca.lab_rank, 0xFF, sizeof(ca.lab_rank));
@@ -2435,7 +2446,7 @@ struct Pipeline {
         ca.n_slots = w.slot_ctr;
         CU(ctx, cudaMemsetAsync(w.slot_ctr, 0, sizeof(unsigned int), s));
         launches++;
-        k_compact_fill<<<grid_for(ctx, n_chunk * 32 + n_med + n_small, 256, 8), 256, 0, s>>>(ca);
+        k_compact_fill<<<grid_for(ctx, listed * 32, 256, 8), 256, 0, s>>>(ca);
         CU(ctx, cudaGetLastError());
         launches++;
         k_compact_bits<<<grid_for(ctx, last_kept / 32 + 2, 256, 8), 256, 0, s>>>(w.sub_bits[nb], w.sub_rp[nb] + g->n);
@@ -2774,6 +2785,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         return fail(set_err(ctx, CCPM_EOVERFLOW, "hub bookkeeping overflow"));
 
     // ---- LCC to fixpoint (Alg. 4)
+    P.searches_ahead = (int)t.order.size();
     int64_t rounds = 0;
     RCF(P.lcc(&rounds));
     r->phase_rounds.push_back((int32_t)rounds);
@@ -2832,6 +2844,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         std::memcpy(lg.features, &feats[pick * CCPM_MLP_IN], sizeof(lg.features));
         lg.bits_before = (int64_t)w.hist_h[kMaxT];
         remaining.erase(remaining.begin() + (long)pick);
+        P.searches_ahead = (int)remaining.size() + 1;
         const HostConstraint &c = t.k0[(size_t)chosen];
         nl_run++;
         if (noop) {
@@ -2909,6 +2922,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             P.ms_search_kernel += ms_k;
         }
         bool changed = n_roots > 0 && w.st_h->changed;
+        P.searches_ahead = (int)remaining.size();
         CUF(cudaEventRecord(w.ev[7], s));
         int64_t rr = 0;
         if (changed) {
@@ -3030,14 +3044,21 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         };
         // count the matches (every match lies inside the pruned state); with
         // few of them one more enumeration that marks each gives omega* and E*
+        // one enumeration that counts and marks, while the matches are few;
+        // past that a counting enumeration up to the cap, then existence passes
         bool capped = false;
-        RCF(count_pass(kCount, w.om[P.cur], opt.max_embeddings, matches, capped));
-        count_valid = !capped;
-        if (!capped && matches <= kMarkCap) {
-            uint64_t again = 0;
-            RCF(count_pass(kMark, w.om[P.cur], opt.max_embeddings, again, capped));
+        const uint64_t mark_cap = std::min<uint64_t>(opt.max_embeddings, kMarkCap);
+        RCF(count_pass(kMark, w.om[P.cur], mark_cap, matches, capped));
+        if (!capped) {
+            count_valid = true;
             final_done = true;
         } else {
+            if (opt.max_embeddings > kMarkCap) {
+                RCF(count_pass(kCount, w.om[P.cur], opt.max_embeddings, matches, capped));
+                count_valid = !capped;
+            } else {
+                count_valid = false;
+            }
             CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
             CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
             a.om_out = nullptr;
