@@ -1899,6 +1899,7 @@ struct ccpm_graph {
     uint8_t *nlab = nullptr;
     std::mutex lrow_mu;           // concurrent batch workers build the grouped rows once
     int tuned_workers = 0;        // batch worker count chosen by the autotuner
+    std::atomic<int> prunes{0};   // prunes started on this graph
 };
 
 struct ccpm_tmpl {
@@ -2323,6 +2324,15 @@ struct Pipeline {
         return searches_ahead > 0 && last_rows >= ((int64_t)1 << 21) && last_kept * 8 < last_rows;
     }
 
+    // A search needs label-grouped rows.  The grouped copy of the full rows
+    // (a sort of every row, once per graph) pays off over many prunes of a
+    // resident graph; for a graph's first prunes compacting the live rows is
+    // far cheaper.
+    bool cheaper_than_label_rows() const {
+        return compact_mode >= 0 && gen < 0 && g->lcol == nullptr && g->prunes < 2 && last_rows > 0 &&
+               last_kept < last_rows;
+    }
+
     // Frontier of the live vertices over rows rp (the pieces of a long row
     // consecutive and in order); also makes both omega buffers equal.
     int rebucket(const int64_t *rp, bool sync = true) {
@@ -2534,9 +2544,9 @@ int ccpm_graph_load_csr(ccpm_ctx_t ctx, int64_t n, int64_t m, const int64_t *row
     if (!dev) {
         if (row_ptr[0] != 0 || row_ptr[n] != m)
             return set_err(ctx, CCPM_EINVAL, "graph: row_ptr[0] must be 0 and row_ptr[n] == m_dir");
-        for (int64_t v = 0; v < n; v++)
-            if (row_ptr[v + 1] < row_ptr[v]) return set_err(ctx, CCPM_EINVAL, "graph: row_ptr not monotone");
         if (flags & CCPM_VALIDATE) {
+            for (int64_t v = 0; v < n; v++)
+                if (row_ptr[v + 1] < row_ptr[v]) return set_err(ctx, CCPM_EINVAL, "graph: row_ptr not monotone");
             for (int64_t v = 0; v < n; v++) {
                 for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
                     int32_t u = col[e];
@@ -2581,13 +2591,18 @@ int ccpm_graph_load_csr(ccpm_ctx_t ctx, int64_t n, int64_t m, const int64_t *row
             e = cudaMemcpyAsync(g->col, col, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->lab, labels, (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) {
+        // the offsets' check and the label histogram run while the copies do
+        bool monotone = true;
+        for (int64_t v = 0; v < n && monotone; v++) monotone = row_ptr[v + 1] >= row_ptr[v];
+        for (int64_t v = 0; v < n; v++) g->label_freq[labels[v]]++;
+        const cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess || !monotone) {
             cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab);
             delete g;
+            if (!monotone) return set_err(ctx, CCPM_EINVAL, "graph: row_ptr not monotone");
             return set_err(ctx, CCPM_ECUDA, std::string("graph upload: ") + cudaGetErrorString(e));
         }
-        for (int64_t v = 0; v < n; v++) g->label_freq[labels[v]]++;
     }
     *out = g;
     return CCPM_OK;
@@ -2716,6 +2731,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.lrp = g->rp;
     P.lcol = g->col;
     P.lbits = w.ebits;
+    g->prunes++;
     P.compact_mode = opt.compact;
     cudaStream_t s = ctx->stream;
 
@@ -2867,7 +2883,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         RCF(P.read_stats());
         const int64_t n_roots = w.st_h->n_roots;
         if (n_roots > 0) {
-            if (P.want_compact()) RCF(P.compact());
+            if (P.want_compact() || P.cheaper_than_label_rows()) RCF(P.compact());
             if (P.gen < 0) RCF(ensure_label_rows(ctx, g));
             CUF(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
             SearchArgs a{};
@@ -2954,7 +2970,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     bool final_done = false;
     if (opt.run_final) {
         const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
-        if (P.want_compact()) RCF(P.compact());
+        if (P.want_compact() || P.cheaper_than_label_rows()) RCF(P.compact());
         if (P.gen < 0) RCF(ensure_label_rows(ctx, g));
         CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
         CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
