@@ -108,7 +108,11 @@ typedef struct {
                                    /* most entries of the live rows are inactive,  */
                                    /* 1 = after every round that leaves some, -1 = */
                                    /* never; results are the same in all modes     */
-    int      reserved[5];
+    int      search_split;         /* windows a search scans before it hands its   */
+                                   /* untried candidates to other warps: 0 = the   */
+                                   /* library default (2048), -1 = never; results  */
+                                   /* are the same for every value                 */
+    int      reserved[4];
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 

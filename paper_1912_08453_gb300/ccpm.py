@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("order_mode", ctypes.c_int), ("run_final", ctypes.c_int),
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
-                ("compact", ctypes.c_int), ("reserved", ctypes.c_int * 5),
+                ("compact", ctypes.c_int), ("search_split", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4),
                 ("mlp", ctypes.c_void_p)]
 
 

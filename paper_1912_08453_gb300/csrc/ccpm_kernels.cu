@@ -2108,7 +2108,8 @@ constexpr uint64_t kSpillAfter = 2048;
 // per template position).  kind 0: NLCC existence (k_nlcc_items), 1: final
 // count, 2: final count and mark.  Counting (and marking) stops once the cap
 // is passed.
-int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, int64_t &launches, int64_t &passes) {
+int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t split, int64_t &launches,
+                int64_t &passes) {
     cudaStream_t s = ctx->stream;
     SearchItem *bufs[2] = {w.items, w.spill_items};
     const int64_t caps[2] = {w.items_cap, w.spill_cap};
@@ -2117,7 +2118,7 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, int64_t &l
         a.items = bufs[cur];
         a.spill = bufs[cur ^ 1];
         a.spill_cap = caps[cur ^ 1];
-        a.spill_after = kSpillAfter;
+        a.spill_after = split;
         CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
         CU(ctx, cudaMemsetAsync(&w.st->n_spill, 0, sizeof(unsigned int), s));
         const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
@@ -2693,6 +2694,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     }
     const int hub_deg = opt.hub_degree > 0 ? std::min(opt.hub_degree, kMaxHubDeg) : kDefaultHubDeg;
     const uint64_t budget = opt.search_budget ? opt.search_budget : kDefaultSearchBudget;
+    const uint64_t split = opt.search_split < 0 ? 0 : (opt.search_split == 0 ? kSpillAfter : (uint64_t)opt.search_split);
     int rc = ws_ensure(ctx, g, hub_deg);
     if (rc) return rc;
     Workspace &w = ctx->ws;
@@ -2917,7 +2919,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             CUF(cudaMemcpyAsync(w.aux_h, &w.st->windows, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CUF(cudaEventRecord(w.ev[10], s));
             if (a.n_items <= w.items_cap) {
-                RCF(item_passes(ctx, w, a, 0, P.launches, P.item_passes));
+                RCF(item_passes(ctx, w, a, 0, split, P.launches, P.item_passes));
             } else {
                 P.launches++;
                 k_nlcc_search<<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
@@ -2992,7 +2994,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         a.items_cap = w.items_cap;
         auto run_items = [&](bool edge_pass) -> int {
             if (!edge_pass) {
-                int rc2 = item_passes(ctx, w, a, 0, P.launches, P.item_passes);
+                int rc2 = item_passes(ctx, w, a, 0, split, P.launches, P.item_passes);
                 return rc2 ? rc2 : P.read_stats();
             }
             // edge items keep the entry index in their last two slots: not split further
@@ -3043,7 +3045,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
             const bool use_items = a.n_items <= w.items_cap;
             const int gr = grid_for(ctx, nr * 32, 128, 16);
             if (use_items) {
-                if ((rc2 = item_passes(ctx, w, a, mode == kMark ? 2 : 1, P.launches, P.item_passes))) return rc2;
+                if ((rc2 = item_passes(ctx, w, a, mode == kMark ? 2 : 1, split, P.launches, P.item_passes))) return rc2;
             } else if (mode == kMark) {
                 P.launches++;
                 k_final_search<kMark><<<gr, 128, 0, s>>>(a);
