@@ -32,6 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "template time-to-solution (ms) & edges scanned/s, batched+learned vs plain"
+# "edges scanned" counts the active CSR entries the LCC rounds examine: the
+# same number on every implementation that follows the method (the GPU path
+# and the oracle agree on it bit for bit), so values of different arms compare
+# as time ratios.  Entries examined by the searches depend on how a search is
+# organised and are reported beside it, not in it.
 
 WORKLOADS = {
     "rmat22-degree": {
@@ -171,7 +176,7 @@ def cpu_oracle_run(g, templates, budget_s=30.0):
     done, edges, secs = [], 0, 0.0
     for name, (tl, te) in templates.items():
         r = pipeline.run(g.row_ptr, g.col, g.labels, tl, te)
-        edges += r.lcc_scanned + r.search_scanned
+        edges += r.lcc_scanned
         secs += r.seconds
         done.append(f"{name}: {r.seconds:.1f}s")
         if secs > budget_s:
@@ -188,8 +193,7 @@ def run_reference(args, cfg):
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; nothing to do
     times, edges = [], 0
-    first = next(iter(cfg["templates"].items()))
-    sample = {first[0]: first[1]}
+    sample = dict(cfg["templates"])          # the same templates as the GPU arm's step
     for _ in range(args.steps):
         e, s, _ = cpu_oracle_run(g, sample, budget_s=1e9)
         edges += e
@@ -203,7 +207,7 @@ def run_reference(args, cfg):
             "config": {"workload": args.workload, "scale": cfg["scale"], "n": g.n, "m_dir": g.m_dir,
                        "templates": sorted(sample)},
             "cpu_baseline": {"value": value, "unit": "edges scanned/s", "cores": 1, "kind": "oracle",
-                             "sample": f"template {first[0]} per step, whole pipeline"},
+                             "sample": "every template of the workload per step, whole pipeline"},
             "e2e": {"value": value, "unit": "edges scanned/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -301,7 +305,7 @@ def run_batch_workload(args, cfg):
     same = all(np.array_equal(a.omega(), b.omega()) and np.array_equal(a.edge_bitmap(), b.edge_bitmap())
                and a.counts()["match_embeddings"] == b.counts()["match_embeddings"]
                for a, b in zip(res_plain, res_batch))
-    edges = sum(r.counts()["edges_scanned_lcc"] + r.counts()["edges_scanned_search"] for r in res_batch)
+    edges = sum(r.counts()["edges_scanned_lcc"] for r in res_batch)
     ms_plain, ms_batch = statistics.median(t_plain), statistics.median(t_batch)
     dev = f"cuda:{local}"
     ms_plain, _, _ = sharding.reduce_step(ms_plain, 0, True, device=dev)
@@ -393,7 +397,8 @@ def main():
             step_ms.append(ev0.elapsed_time(ev1))
             agg.append(st)
         clk = clocks.stop()
-    edges = sum(c["edges_scanned_lcc"] + c["edges_scanned_search"] for st in agg for c in st.values())
+    edges = sum(c["edges_scanned_lcc"] for st in agg for c in st.values())
+    search_entries = sum(c["edges_scanned_search"] for st in agg for c in st.values())
     total_ms = sum(step_ms)
     from paper_1912_08453_gb300 import sharding
     total_ms, edges, _ = sharding.reduce_step(total_ms, edges, True, device=f"cuda:{local}")
@@ -442,6 +447,7 @@ def main():
                            "templates": {k: {"labels": v[0], "edges": v[1]} for k, v in cfg["templates"].items()},
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "tts_ms": tts,
+                "search_entries_per_s": search_entries / (total_ms / 1e3) if total_ms > 0 else 0.0,
                 "phases": {k: results[k].phase_rounds() for k in tmpls},
                 "matches": {k: agg[-1][k]["match_embeddings"] for k in tmpls},
                 "roofline": roofline, "rooflines": [roof_lcc, roof_search],
@@ -473,7 +479,7 @@ def run_e2e(args, ctx, g, cfg, tmpls, stream, local):
             r.omega(outs[k][0])
             r.edge_bitmap(outs[k][1])
             c = r.counts()
-            edges += c["edges_scanned_lcc"] + c["edges_scanned_search"]
+            edges += c["edges_scanned_lcc"]
             r.close()
         gr.close()
         return edges
