@@ -1900,6 +1900,7 @@ struct ccpm_graph {
     std::mutex lrow_mu;           // concurrent batch workers build the grouped rows once
     int tuned_workers = 0;        // batch worker count chosen by the autotuner
     std::atomic<int> prunes{0};   // prunes started on this graph
+    std::atomic<bool> lrows_ready{false};   // lcol/nlab built (read without the lock)
 };
 
 struct ccpm_tmpl {
@@ -2059,6 +2060,7 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
         return set_err(ctx, e == cudaErrorMemoryAllocation ? CCPM_ENOMEM : CCPM_ECUDA,
                        std::string("label-grouped rows: ") + cudaGetErrorString(e));
     }
+    g->lrows_ready.store(true);
     return CCPM_OK;
 }
 
@@ -2330,7 +2332,7 @@ struct Pipeline {
     // resident graph; for a graph's first prunes compacting the live rows is
     // far cheaper.
     bool cheaper_than_label_rows() const {
-        return compact_mode >= 0 && gen < 0 && g->lcol == nullptr && g->prunes < 2 && last_rows > 0 &&
+        return compact_mode >= 0 && gen < 0 && !g->lrows_ready.load() && g->prunes < 2 && last_rows > 0 &&
                last_kept < last_rows;
     }
 

@@ -415,3 +415,38 @@ def test_scanned_counts_active_entries():
     expect = int(np.sum(A[(om[src] != 0)]))
     _, _, _, sc = oracle.lcc_round(og, tl, te, om, A)
     assert sc == expect
+
+
+def _compat_state(g, tl, te, om):
+    """[both ends live and compat(omega(v), omega(u))] per CSR entry (eta of
+    Alg. 4, written out from the template's adjacency)."""
+    adj = [0] * len(tl)
+    for a, b in te:
+        adj[a] |= 1 << b
+        adj[b] |= 1 << a
+    nbr = np.zeros(len(om), dtype=np.uint64)
+    for q in range(len(tl)):
+        nbr |= np.where((om.astype(np.uint64) >> np.uint64(q)) & np.uint64(1), np.uint64(adj[q]), np.uint64(0))
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    omu = om.astype(np.uint64)
+    return ((omu[src] != 0) & (omu[g.col] != 0) & ((nbr[src] & omu[g.col]) != 0)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("tname,tl,te", TEMPLATES[:8], ids=[t[0] for t in TEMPLATES[:8]])
+def test_fixpoint_edges_are_compat_on_live_pairs(seed, tname, tl, te):
+    """At every LCC fixpoint (after the first LCC and after each non-local
+    constraint's re-run) an entry is active exactly when both ends are live
+    and their omegas are compatible: bits are cleared only by a failed eta or
+    a dead end, and eta stays true once omega only shrinks.  The searches
+    rely on this instead of reading the edge flags."""
+    g = random_graph(900 + seed, 32, 0.25, max(tl) + 1)
+    og = oracle.Graph(g.row_ptr, g.col, g.labels)
+    om, A = oracle.init(og, tl, te)
+    oracle.lcc(og, tl, te, om, A)
+    np.testing.assert_array_equal(A, _compat_state(g, tl, te, om))
+    for c in cgen.generate(tl, te):
+        ch, _ = oracle.nlcc(og, c.vmask(), c.sadj(len(tl)), c.hmask(), om, A)
+        if ch:
+            oracle.lcc(og, tl, te, om, A)
+        np.testing.assert_array_equal(A, _compat_state(g, tl, te, om))
