@@ -545,8 +545,9 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 a.om_next[v] = keep;
                 if (a.deg) a.deg[v] = keep ? (int64_t)p_nN : 0;
             }
-            bm.push(lane == 0 && wv != 0u, v);
         }
+        // the chunk's vertices that were active at the start of the round, in one push
+        bm.push(vl >= 0 && wl != 0u, vl);
     }
 
     // (3) short rows: 4 lanes per vertex, 8 vertices per warp step; the list
@@ -588,8 +589,8 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 a.om_next[v] = keep;
                 if (a.deg) a.deg[v] = keep ? (int64_t)p.nN : 0;
             }
-            bs.push(lg == 0 && wv != 0u, v);
         }
+        bs.push(vl >= 0 && wl != 0u, vl);
     }
 
     bs.flush();
