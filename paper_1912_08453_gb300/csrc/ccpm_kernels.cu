@@ -56,7 +56,9 @@ struct RoundStats {
     unsigned int n_roots;
     unsigned int n_items;         // (root, head, first candidate) search items
     unsigned int overflow;        // a search hit its budget
-    unsigned int n_spill;         // items handed on by searches that ran long
+    unsigned int n_spill;         // items handed on by searches that ran long (reserved)
+    unsigned int spill_stop;      // the spill list is valid below this index (see spill)
+    unsigned int pad2;
 };
 
 struct HubAcc {                   // partial LCC state of one split row
@@ -1225,7 +1227,10 @@ constexpr int kExist = 0, kCount = 1, kMark = 2;
 // (psi[0..L-1], c) of depth L+1 in the spill list; for counting, candidates
 // of the last position are counted here instead.  The items are counted
 // first and written only if they all fit.  Returns false (the search goes on
-// where it is) when they do not.
+// where it is) when they do not.  Reservations only ever add to the counter:
+// the successful ones are exactly those ending at or below the capacity, and
+// they fill the list up to the lowest start of a failed one (spill_stop), so
+// the list is valid below min(counter, spill_stop).
 template <int MODE>
 __device__ bool spill(const SearchArgs &a, const DevPlan &P, WarpSearch &W, int d0, int d,
                       unsigned long long &matches) {
@@ -1245,10 +1250,14 @@ __device__ bool spill(const SearchArgs &a, const DevPlan &P, WarpSearch &W, int 
     unsigned long long base = 0;
     unsigned int fits = 1;
     if (lane == 0 && total) {
-        base = atomicAdd(&a.st->n_spill, (unsigned int)total);
-        if (base + total > (unsigned long long)a.spill_cap) {
-            atomicSub(&a.st->n_spill, (unsigned int)total);
-            fits = 0;
+        if (*(volatile const unsigned int *)&a.st->n_spill >= (unsigned long long)a.spill_cap) {
+            fits = 0;                               // full already: do not grow the counter
+        } else {
+            base = atomicAdd(&a.st->n_spill, (unsigned int)total);
+            if (base + total > (unsigned long long)a.spill_cap) {
+                atomicMin(&a.st->spill_stop, (unsigned int)base);
+                fits = 0;
+            }
         }
     }
     if (!__shfl_sync(FULL_MASK, fits, 0)) return false;
@@ -1520,6 +1529,7 @@ __device__ __forceinline__ int64_t grab_items(const SearchArgs &a, int batch) {
 constexpr int kItemBatch = 4;
 constexpr int kMaxPlans = 64;      // plan slots (heads, or oriented template edges)
 constexpr uint64_t kMarkCap = 1ull << 20;   // matches one marking enumeration handles
+constexpr uint64_t kFewMatches = 1ull << 16;   // marked during the first enumeration itself
 // Below this many first-level items the searches place position 2 as well.
 constexpr int64_t kExpandBelow = 16384;
 
@@ -2124,6 +2134,7 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t s
         a.spill_after = split;
         CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
         CU(ctx, cudaMemsetAsync(&w.st->n_spill, 0, sizeof(unsigned int), s));
+        CU(ctx, cudaMemsetAsync(&w.st->spill_stop, 0xFF, sizeof(unsigned int), s));
         const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
         launches++;
         passes++;
@@ -2133,8 +2144,10 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t s
         CU(ctx, cudaGetLastError());
         CU(ctx, cudaMemcpyAsync(&w.aux_h[1], &w.st->n_spill, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaMemcpyAsync(&w.aux_h[2], &w.st->overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaMemcpyAsync(&w.aux_h[3], &w.st->spill_stop, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
-        const unsigned int spilled = (unsigned int)(w.aux_h[1] & 0xFFFFFFFFull);
+        const unsigned int spilled = std::min((unsigned int)(w.aux_h[1] & 0xFFFFFFFFull),
+                                              (unsigned int)(w.aux_h[3] & 0xFFFFFFFFull));
         const unsigned int over = (unsigned int)(w.aux_h[2] & 0xFFFFFFFFull);
         if (spilled == 0 || (kind != 0 && over)) break;
         a.n_items = spilled;
@@ -2319,13 +2332,15 @@ struct Pipeline {
 
     // Compact when most entries of the live rows are inactive: the next round
     // (or search) would mostly skip them.
-    // Automatic mode compacts only while non-local constraints are still to
-    // run: their searches gain the most, while the LCC rounds alone barely pay
-    // for the copy (measured on the scale-22 tree template).
-    bool want_compact() const {
+    // Automatic mode compacts for searches: while non-local constraints are
+    // still to run, and before the final search.  The LCC rounds alone barely
+    // pay for the copy (measured on the scale-22 tree template), so an
+    // LCC-only template is not compacted between its rounds.
+    bool want_compact(bool final_search = false) const {
         if (compact_mode < 0 || last_rows <= 0) return false;
         if (compact_mode > 0) return last_kept < last_rows;
-        return searches_ahead > 0 && last_rows >= ((int64_t)1 << 21) && last_kept * 8 < last_rows;
+        return (final_search || searches_ahead > 0) && last_rows >= ((int64_t)1 << 21) &&
+               last_kept * 8 < last_rows;
     }
 
     // A search needs label-grouped rows.  The grouped copy of the full rows
@@ -2975,7 +2990,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     bool final_done = false;
     if (opt.run_final) {
         const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
-        if (P.want_compact() || P.cheaper_than_label_rows()) RCF(P.compact());
+        if (P.want_compact(true) || P.cheaper_than_label_rows()) RCF(P.compact());
         if (P.gen < 0) RCF(ensure_label_rows(ctx, g));
         CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
         CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
@@ -3065,21 +3080,29 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         };
         // count the matches (every match lies inside the pruned state); with
         // few of them one more enumeration that marks each gives omega* and E*
-        // one enumeration that counts and marks, while the matches are few;
-        // past that a counting enumeration up to the cap, then existence passes
+        // few matches (at most kFewMatches): one enumeration counts and marks
+        // them.  More: a counting enumeration up to the cap; then, up to
+        // kMarkCap matches, one more enumeration marks them, and past that the
+        // existence passes answer omega* and E*.
         bool capped = false;
-        const uint64_t mark_cap = std::min<uint64_t>(opt.max_embeddings, kMarkCap);
-        RCF(count_pass(kMark, w.om[P.cur], mark_cap, matches, capped));
+        RCF(count_pass(kMark, w.om[P.cur], std::min<uint64_t>(opt.max_embeddings, kFewMatches), matches, capped));
         if (!capped) {
             count_valid = true;
             final_done = true;
-        } else {
-            if (opt.max_embeddings > kMarkCap) {
-                RCF(count_pass(kCount, w.om[P.cur], opt.max_embeddings, matches, capped));
-                count_valid = !capped;
-            } else {
-                count_valid = false;
+        } else if (opt.max_embeddings > kFewMatches) {
+            RCF(count_pass(kCount, w.om[P.cur], opt.max_embeddings, matches, capped));
+            count_valid = !capped;
+            if (!capped && matches <= kMarkCap) {
+                uint64_t again = 0;
+                CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
+                CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
+                RCF(count_pass(kMark, w.om[P.cur], opt.max_embeddings, again, capped));
+                final_done = true;
             }
+        } else {
+            count_valid = false;
+        }
+        if (!final_done) {
             CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
             CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
             a.om_out = nullptr;
