@@ -214,7 +214,9 @@ def run_reference(args, cfg):
 
 
 def graph_workers(graph):
-    return None
+    """Worker count the batch autotuner chose for this graph."""
+    from paper_1912_08453_gb300 import ccpm
+    return int(ccpm.lib.ccpm_graph_batch_workers(graph.h))
 
 
 def batch_templates(cfg):

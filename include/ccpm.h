@@ -234,6 +234,9 @@ int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
  * (see each result's counts), or the first error. */
 int  ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *tmpls,
                       const ccpm_options *opt, ccpm_result_t *outs);
+/* The worker count the autotuner chose for batches over g (0 before the first
+ * autotuned ccpm_prune_batch call, or with NULL). */
+int  ccpm_graph_batch_workers(ccpm_graph_t g);
 
 /* ----------------------------------------------------------------- result */
 

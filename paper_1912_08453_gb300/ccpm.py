@@ -114,6 +114,7 @@ def _load():
         "ccpm_mlp_forward": ([vp, i32, vp, vp], i32),
         "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
         "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
+        "ccpm_graph_batch_workers": ([vp], i32),
         "ccpm_state_export": ([vp, vp, P(ctypes.c_size_t)], i32),
         "ccpm_state_import": ([vp, vp, vp, vp, ctypes.c_size_t, P(vp)], i32),
         "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
@@ -137,7 +138,7 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc",
             "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
             "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train",
-            "ccpm_state_export", "ccpm_state_import"]
+            "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers"]
 
 
 def _ptr(a):

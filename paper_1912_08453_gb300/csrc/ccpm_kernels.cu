@@ -3382,6 +3382,8 @@ int ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap) {
 const uint32_t *ccpm_result_omega_device(ccpm_result_t r) { return r ? r->om : nullptr; }
 const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r) { return r ? r->eb : nullptr; }
 
+int ccpm_graph_batch_workers(ccpm_graph_t g) { return g ? g->tuned_workers : 0; }
+
 void ccpm_result_destroy(ccpm_result_t r) {
     if (!r) return;
     cudaSetDevice(r->g->ctx->device);
