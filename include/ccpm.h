@@ -7,7 +7,7 @@
  * Metadata Graphs via Constraint Checking"): local constraint checking to a
  * fixpoint (Alg. 4), one non-local constraint at a time with LCC re-run after
  * any change (Alg. 1, Alg. 6/7), and a final template-driven search over the
- * whole template (Remark 1, Section 4.6) that also counts matches.
+ * whole template (Remark 1, Section 4.7) that also counts matches.
  *
  * Conventions
  *   - Every call returns an int status (CCPM_OK or a CCPM_E* code); no C++
@@ -16,7 +16,7 @@
  *     in both rows; row_ptr is int64 [n+1], col is int32 [m_dir] with every row
  *     sorted ascending, no self loops, no duplicates.  labels is uint8 [n].
  *   - omega layout: uint32 per vertex; bit q set <=> template vertex q is a
- *     possible match of that vertex (omega(v) of Section 2).
+ *     possible match of that vertex (omega(v) of Section 3).
  *   - Edge bitmap layout: one bit per CSR entry e, bit (e & 31) of word e >> 5
  *     (uint32 words, ceil(m_dir / 32) of them); both directions of an
  *     undirected edge always carry the same value.
@@ -61,7 +61,7 @@ extern "C" {
 #define CCPM_KIND_TDS_PC 3
 #define CCPM_KIND_TDS    4
 
-/* constraint order (Section 3.2 "Constraint Ordering Heuristics") */
+/* constraint order (Section 4.2 "Constraint Ordering Heuristics") */
 #define CCPM_ORDER_FIXED    0  /* the paper's heuristic: paths and cycles first, shorter first */
 #define CCPM_ORDER_EXPLICIT 1  /* the order given by ccpm_tmpl_set_order                       */
 #define CCPM_ORDER_LEARNED  2  /* before each constraint, the remaining ones are scored by the
@@ -176,8 +176,8 @@ void ccpm_options_default(ccpm_options *opt);
 
 /* ------------------------------------------------------------------ graph */
 
-/* Load the background graph G (Section 2; CSR + separate label store as in
- * Section 4.7).  n vertices, m_dir directed CSR entries.  With
+/* Load the background graph G (Section 3; CSR + separate label store as in
+ * Section 4.8).  n vertices, m_dir directed CSR entries.  With
  * CCPM_HOST_PTRS the arrays are copied to the device; with CCPM_DEVICE_PTRS
  * they are borrowed.  CCPM_VALIDATE adds an O(m) host check (host pointers
  * only) and returns CCPM_EINVAL on an unsorted row, self loop, duplicate or a
@@ -189,17 +189,17 @@ void ccpm_graph_destroy(ccpm_graph_t g);
 
 /* --------------------------------------------------------------- template */
 
-/* Load template G0 (Section 2): n0 in [2, 32] vertices with labels, m0
+/* Load template G0 (Section 3): n0 in [2, 32] vertices with labels, m0
  * undirected edges given as 2*m0 int32 (a, b) pairs.  CCPM_EINVAL if G0 is
- * disconnected (Section 2 assumes connected), has a self loop, a duplicate or
+ * disconnected (Section 3 assumes connected), has a self loop, a duplicate or
  * an out-of-range vertex. */
 int  ccpm_tmpl_load(ccpm_ctx_t ctx, int n0, const uint8_t *labels, int m0,
                     const int32_t *edges, ccpm_tmpl_t *out);
 void ccpm_tmpl_destroy(ccpm_tmpl_t t);
 
 /* Generate the ordered non-local constraint set K0 (Table 3 Steps 1-5,
- * Alg. 2, ordering of Section 3.2).  The graph supplies background label
- * frequencies used to orient token walks (Section 3.2 "Constraint
+ * Alg. 2, ordering of Section 4.2).  The graph supplies background label
+ * frequencies used to orient token walks (Section 4.2 "Constraint
  * Optimization"); it may be NULL.  Writes |K0| to *n_constraints. */
 int  ccpm_constraints_generate(ccpm_tmpl_t t, ccpm_graph_t g, int *n_constraints);
 /* Describe constraint i (0-based, in the current order). */
@@ -223,7 +223,7 @@ int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
                 const ccpm_options *opt, ccpm_result_t *out);
 
 /* Prune T templates over the same resident graph (the exploratory-search
- * workload of Section 7.2: many variants of one query).  Each template's
+ * workload of Section 6.7: many variants of one query).  Each template's
  * results are exactly those ccpm_prune gives for it.  The templates run
  * concurrently on worker streams of this context, each with its own scratch,
  * so that small phases of different templates overlap on the GPU; the number
@@ -274,7 +274,7 @@ void ccpm_result_destroy(ccpm_result_t r);
  * ccpm_state_import: checks the blob against g and t (CCPM_EINVAL on a wrong
  * magic, version, size, fingerprint or checksum) and returns a new result in
  * *out holding that state, owned by the caller like any result.  Pruning
- * removes only candidates that no match uses (Section 3), so any state this
+ * removes only candidates that no match uses (Section 4), so any state this
  * library produced for (g, t) contains every match; ccpm_prune with
  * options.resume = 1 continues from it (LCC, the non-local constraints and
  * the final search) and ends in the same omega*, E* and match count as a
@@ -287,7 +287,7 @@ int  ccpm_state_import(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t, const void
 
 /* A 3-layer perceptron that scores non-local constraints for
  * CCPM_ORDER_LEARNED (the paper orders constraints by a fixed heuristic,
- * Section 3.2, and leaves learned orders to future work, Section 9).
+ * Section 4.2, and leaves learned orders to future work, Section 8).
  * Parameters: FP32 master copy of CCPM_MLP_PARAMS floats laid out as
  * W1[16][64], b1[64], W2[64][64], b2[64], w3[64], b3 (W[i][j]: input i to
  * unit j).  Products run on BF16 tensor cores with FP32 accumulation:

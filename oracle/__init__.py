@@ -7,7 +7,7 @@ binding) never does, and it shares no code with it.
 * `ccpm_oracle.c`  -- plain single-threaded C: init (Alg. 3), one LCC round and
   the LCC fixpoint (Alg. 4/5), one NLCC constraint (Alg. 6/7, as an injective
   rooted-embedding search), final template-driven search with match counting
-  (Remark 1, Section 4.6).
+  (Remark 1, Section 4.7).
 * `constraints.py` -- non-local constraint generation (Table 3, Alg. 2).
 * `pipeline.py`    -- the main loop (Alg. 1) over the pieces above.
 """

@@ -80,7 +80,7 @@ static int compatible(int n0, const uint32_t *tadj, uint32_t wv, uint32_t wu)
 /*  - q stays in omega(v) iff adj(q) is a subset of omega' and, for every    */
 /*    label L, at least |adj_L(q)| distinct surviving neighbours u have      */
 /*    omega(u) meeting adj_L(q) (the "minimum number of distinct active      */
-/*    neighbours with the same label", Section 3.1 and Section 4.1)          */
+/*    neighbours with the same label", Section 4.1 and Section 4.3)          */
 /*  - v is eliminated if omega(v) or its active edge map becomes empty.      */
 /* Finally an entry is dropped if either endpoint was eliminated.            */
 /* Returns 1 if omega or A changed.  *scanned += active entries read.        */
@@ -329,7 +329,7 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Final template-driven search on the pruned graph (Remark 1; Section 4.6:  */
+/* Final template-driven search on the pruned graph (Remark 1; Section 4.7:  */
 /* the walk covers the full template, work aggregation off, every match      */
 /* verified).  Enumerates every injective phi with q in omega(phi(q)) and an  */
 /* active edge for every template edge.  Outputs: om_out[v] = {q : some match */

@@ -1,7 +1,7 @@
 """Non-local constraint generation for the oracle (TEST INFRASTRUCTURE).
 
 Plain Python restatement of the paper's Table 3 procedure (Steps 1-5) and of
-Alg. 2 (TDS_CONSTRAINTS), with the ordering heuristic of Section 3.2
+Alg. 2 (TDS_CONSTRAINTS), with the ordering heuristic of Section 4.2
 ("Constraint Ordering Heuristics").  Shares no code with the product's C++
 constraint generator; the tests compare the two lists element by element.
 
@@ -23,7 +23,7 @@ design notes):
     edge set) removed, first occurrence kept; then stably ordered by
     (is TDS, number of edges, kind rank PC < CC < TDS_CC < TDS_PC < TDS,
     generation index).
-  * Heads (Section 3.2 "Token Generation"): every vertex of a cycle or of a
+  * Heads (Section 4.2 "Token Generation"): every vertex of a cycle or of a
     cycle-derived TDS; both terminals of a path; for path-derived and mixed TDS
     the vertices of S whose label repeats in the template (all of S if none).
 """

@@ -3,7 +3,7 @@
 init (Alg. 3) -> LCC to fixpoint (Alg. 4) -> for each non-local constraint in
 order: NLCC (Alg. 6/7), and LCC again if any omega changed (Alg. 1) -> final
 template-driven search over the full template, which also counts matches
-(Remark 1; Section 4.6).
+(Remark 1; Section 4.7).
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
 // ccpm_host.cpp -- host-side template logic: validation, non-local constraint
-// generation (Table 3 Steps 1-5 with Alg. 2, ordering of Section 3.2),
+// generation (Table 3 Steps 1-5 with Alg. 2, ordering of Section 4.2),
 // label-preserving automorphisms, and the search plans the kernels walk.
 //
 // Everything here is integer work on a template of at most 32 vertices; it runs
@@ -294,7 +294,7 @@ int constraints_generate(Template &t, std::string &err) {
             c.vmask = s.v;
             c.edges.assign(s.e.begin(), s.e.end());
             c.gen_index = (int)k0.size();
-            // token issuers (Section 3.2 "Token Generation")
+            // token issuers (Section 4.2 "Token Generation")
             if (kind == CCPM_KIND_CC || kind == CCPM_KIND_TDS_CC) {
                 c.hmask = s.v;
             } else if (kind == CCPM_KIND_PC) {
@@ -318,7 +318,7 @@ int constraints_generate(Template &t, std::string &err) {
     add(tcc, CCPM_KIND_TDS_CC);
     add(tpc, CCPM_KIND_TDS_PC);
     add(tds, CCPM_KIND_TDS);
-    // Section 3.2: paths and cycles before TDS, shorter walks first.
+    // Section 4.2: paths and cycles before TDS, shorter walks first.
     std::stable_sort(k0.begin(), k0.end(), [](const HostConstraint &a, const HostConstraint &b) {
         int ta = a.kind >= CCPM_KIND_TDS_CC, tb = b.kind >= CCPM_KIND_TDS_CC;
         if (ta != tb) return ta < tb;

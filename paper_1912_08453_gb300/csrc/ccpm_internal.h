@@ -19,7 +19,7 @@ constexpr uint64_t kDefaultSearchBudget = 1ull << 22;
 
 // Template tables for the LCC kernels.  A "class" is (q, L) with
 // |adj_L(q)| >= 2: vertex q of the template needs at least `need` distinct
-// active neighbours whose omega meets `mask` = adj_L(q) (Section 3.1 / 4.1).
+// active neighbours whose omega meets `mask` = adj_L(q) (Section 4.1 / Section 4.3).
 struct DevTmpl {
     int n0;
     int n_cls;

@@ -403,7 +403,7 @@ __device__ __forceinline__ void clear_rel(uint32_t *ebits, int64_t beg, uint32_t
 }
 
 // The vertex-elimination rule of Alg. 4 plus the multiplicity rule of
-// Section 3.1: q survives iff adj(q) is inside omega' and every class of q
+// Section 4.1: q survives iff adj(q) is inside omega' and every class of q
 // has enough distinct neighbours; no surviving edge eliminates the vertex.
 template <int MAXC>
 __device__ __forceinline__ uint32_t decide(uint32_t wv, const Partial<MAXC> &p, const SmemTmpl &s) {
@@ -2982,7 +2982,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     }
     CUF(cudaEventRecord(w.ev[2], s));
 
-    // ---- final template-driven search and match count (Remark 1, Sec. 4.6)
+    // ---- final template-driven search and match count (Remark 1, Sec. 4.7)
     // omega* and E* are existence questions answered exactly by searches over
     // the whole template; the number of matches is counted separately.
     bool count_valid = false;

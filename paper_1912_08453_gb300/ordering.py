@@ -1,6 +1,6 @@
 """Learned ordering of non-local constraints: data, training and evaluation.
 
-The plain pipeline (fixed order, Section 3.2) logs, for every constraint it
+The plain pipeline (fixed order, Section 4.2) logs, for every constraint it
 checks, the ordering features in the state where it was chosen, the omega bits
 it removed (with its LCC re-run) and its device time.  The network learns
     target = -log2(1 + microseconds spent)

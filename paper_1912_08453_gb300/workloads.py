@@ -4,7 +4,7 @@ This module only *generates inputs*; it holds none of the pruning arithmetic, so
 both the CUDA path and the CPU oracle consume its arrays unchanged.
 
 Background graphs follow the R-MAT recipe the paper uses for its synthetic runs
-(Section 6 "Datasets", and Section 6.8 for the three (A, B, C, D) skews):
+(Section 6 "Datasets", and Section 6.10 for the three (A, B, C, D) skews):
 2^scale vertices, edge factor 16 directed draws, undirected by storing both
 directions, with self loops and duplicate edges removed.  Vertex labels are
 either degree-derived, l(v) = ceil(log2(d(v)+1)) (Section 6 "Datasets"), which
@@ -225,7 +225,7 @@ def random_template(seed: int, n0: int, extra_edges: int, label_pool,
 def edit_variants(base: Template, count: int, seed: int, label_pool,
                   max_k: int = 2, n_min: int = 5, n_max: int = 9):
     """Edit-distance variants of `base` for the exploratory-search workload
-    (Section 7.2): each variant applies k in {1, 2} random edits drawn from
+    (Section 6.7): each variant applies k in {1, 2} random edits drawn from
     {delete an edge keeping the template connected, add an edge, delete a
     leaf, add a leaf}.  Variants keep 5..9 vertices; duplicates are allowed."""
     rng = _rng(seed)

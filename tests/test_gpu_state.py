@@ -1,7 +1,7 @@
 """Checkpoint/resume through the C ABI: ccpm_state_export / ccpm_state_import
 and ccpm_prune with options.resume.
 
-Pruning only removes candidates that no match uses (Section 3), so a saved
+Pruning only removes candidates that no match uses (Section 4), so a saved
 state of the same graph and template contains every match and a prune resumed
 from it must end in the same omega*, E* and match count as a fresh run (and as
 the oracle).
