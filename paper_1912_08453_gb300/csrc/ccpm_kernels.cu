@@ -11,7 +11,10 @@
 // cleared lazily: the next round sees omega(u) = 0, treats the entry as
 // inactive and clears the bit.  Rows of eliminated vertices are zeroed when
 // they die; rows of vertices that never become active are zeroed only when
-// the edge bitmap is handed back without the final search.
+// the edge bitmap is handed back without the final search.  Once the rows are
+// compacted (K4) the rounds read the compacted rows and their own bitmap; the
+// full bitmap is then frozen and handed back in its fixpoint form (bit, both
+// ends live, compatible omegas).
 #include <cuda_runtime.h>
 
 #include <algorithm>
