@@ -147,13 +147,14 @@ typedef struct {
     int64_t  edges_scanned_search; /* CSR entries examined by NLCC + final search */
     double   ms_total, ms_lcc, ms_nlcc, ms_final;   /* device time per stage     */
     /* measurement of the LCC round kernel (CUDA events around each launch on
-     * the context stream) and its algorithmic traffic:
-     *   24 B per active vertex (two int64 row offsets, omega read and write)
-     * + 4.125 B per CSR entry of an active row (column index, edge bit)
-     * + 4 B per active entry (gather of the neighbour's omega)              */
+     * the context stream) and the traffic the method itself needs per round
+     * (Alg. 4 over n_a active vertices and M_a active CSR entries):
+     *   16 B per active vertex (two 4-byte row offsets, omega read and write)
+     * + 8.25 B per active entry (column index, gather of the neighbour's
+     *   omega, read and write of its edge bit)                              */
     int64_t  lcc_launches;
     double   ms_lcc_kernel;
-    int64_t  lcc_alg_bytes;
+    int64_t  lcc_alg_bytes;        /* sum over rounds of 8.25 M_a + 16 n_a      */
     int64_t  lcc_row_entries;      /* CSR entries in rows of active vertices  */
     int64_t  lcc_active_vertices;  /* active vertices, summed over rounds      */
     int64_t  kernel_launches;      /* all kernels this call launched          */
@@ -161,6 +162,16 @@ typedef struct {
     double   ms_search_kernel;     /* device time of the NLCC search kernels  */
     int64_t  search_launches;      /* their launches                          */
     int64_t  search_entries_nlcc;  /* row entries those kernels examined      */
+    /* what the kernel itself reads and writes per round: 24 B per active
+     * vertex (two int64 offsets, omega read and write) + 4.125 B per entry of
+     * an active row (column index, edge bit) + 4 B per active entry (gather) */
+    int64_t  lcc_kernel_bytes;
+    int64_t  lcc_first_entries;    /* M_a of the first round after init       */
+    double   ms_lcc_first;         /* device time of that round               */
+    /* device time of the final step's parts: the enumerations that count (and
+     * mark) matches, the per-(vertex, template vertex) existence searches and
+     * the per-entry existence searches (both only when the count is capped)  */
+    double   ms_final_count, ms_final_vertex, ms_final_edge;
 } ccpm_counts;
 
 /* ---------------------------------------------------------------- context */
@@ -249,6 +260,64 @@ int  ccpm_result_counts(ccpm_result_t r, ccpm_counts *out);
 /* LCC rounds per phase: [initial LCC, after constraint 1, ...]; a phase whose
  * constraint changed nothing has 0 rounds.  Writes min(cap, n_phases). */
 int  ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap);
+/* Every match of the template within a result of this graph and template
+ * (the listing and the per-vertex / per-edge participation counts that the
+ * Introduction names as what pruning is for; Section 4.7: the full-template
+ * search verifies each match).  A match phi is an injective, label-preserving
+ * map of the template vertices that sends every template edge onto a graph
+ * edge (Definition 1); all matches lie inside the pruned state, so the search
+ * runs only there (on omega of the result; the final state is the fastest).
+ *   list           n0 int32 per match: phi(0), ..., phi(n0-1); the first
+ *                  min(*n_matches, list_cap) matches found, in no set order
+ *                  (nullable when list_cap == 0)
+ *   vertex_counts  uint64 [n] (nullable): matches that contain the vertex
+ *   entry_counts   uint64 [m_dir] (nullable): matches that map a template edge
+ *                  onto the edge of that CSR entry (both entries of an edge
+ *                  get the same count)
+ *   *n_matches     the number of matches (all of them, beyond list_cap too)
+ * Outputs are device pointers on the context's device if dst_on_device, else
+ * host memory (staged through temporary device buffers).  `opt` (nullable):
+ * search_budget bounds the windows one search may scan (0: unbounded),
+ * search_split as for ccpm_prune.  Errors: CCPM_EINVAL for a result of another
+ * graph, template or device; CCPM_EBUDGET if a search ran out of its budget
+ * (the outputs are then incomplete); CCPM_ENOMEM / CCPM_ECUDA. */
+/* Exploratory search (Section 6.7, "Exploratory Search"; "Interactive
+ * Incremental Search" for the candidate set): the base template is relaxed
+ * level by level, level k holding every variant with k template edges
+ * removed that stays connected (vertices and labels are kept, so template
+ * vertex q means the same in every variant); the search stops after the
+ * first level at which some variant has a match.
+ * First the candidate set is built with local constraints only: the union of
+ * the LCC fixpoints of every variant up to max_removed, which holds every
+ * match of every variant.  Each variant is then pruned from the candidate set
+ * (as with options.resume) instead of from the label-initial state; its omega*,
+ * E* and count equal those of a prune of that variant alone.
+ *   variants   per variant examined, in level order (nullable if variants_cap
+ *              is 0): its level, the removed edges (bit i = edge i of the base
+ *              in input order), |V*|, E* entries, count, status, time
+ *   *out       the union of omega* and of E* over the variants with a match at
+ *              the first such level (a new result, or one of this graph to
+ *              reuse); all zero, and *level_found = -1, if no variant up to
+ *              max_removed has a match.  ccpm_result_counts gives its active_v
+ *              and active_e_dir only.
+ * `opt` (nullable) applies to every variant's prune.  The base template may
+ * have at most 64 edges.  Errors as for ccpm_prune; CCPM_EBUDGET if any
+ * variant's prune hit a budget (its outputs are then supersets). */
+typedef struct {
+    int32_t  level;              /* template edges removed                     */
+    int32_t  n_edges;            /* edges of the variant                       */
+    uint64_t removed;            /* bit i: edge i of the base removed          */
+    int64_t  active_v, active_e_dir;
+    uint64_t match_embeddings;
+    int32_t  count_valid, status;
+    double   ms_total;
+} ccpm_explore_variant;
+int  ccpm_explore(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t base, int max_removed, const ccpm_options *opt,
+                  ccpm_explore_variant *variants, int variants_cap, int *n_variants, int *level_found,
+                  double *ms_candidates, ccpm_result_t *out);
+int  ccpm_result_matches(ccpm_ctx_t ctx, ccpm_result_t r, ccpm_tmpl_t t, const ccpm_options *opt,
+                         int32_t *list, uint64_t list_cap, uint64_t *vertex_counts, uint64_t *entry_counts,
+                         int dst_on_device, uint64_t *n_matches);
 /* Device pointers owned by the result (valid until it is destroyed). */
 /* Log record of the i-th constraint in the order it ran (0 <= i < n_phases-1). */
 int  ccpm_result_constraint_log(ccpm_result_t r, int i, ccpm_constraint_log *out);
@@ -334,7 +403,10 @@ int  ccpm_mlp_train(ccpm_mlp_t m, int N, const float *x, const float *t, int ste
  * bytes, written by every call).  The first call on a device looks up the
  * area's device address (make that first call before any stream capture).
  * All calls share the one area: calls whose GPU work overlaps in time, on any
- * streams, corrupt each other's results, so serialise them. */
+ * streams, corrupt each other's results, so serialise them.  The call reads
+ * row_ptr[0] and row_ptr[n] first and returns CCPM_EINVAL unless they are 0
+ * and m_dir.  It makes `device` current while it runs and makes the caller's
+ * current device current again before it returns. */
 int  ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t n, int64_t m_dir,
                                const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
                                int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,

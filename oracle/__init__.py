@@ -7,7 +7,8 @@ binding) never does, and it shares no code with it.
 * `ccpm_oracle.c`  -- plain single-threaded C: init (Alg. 3), one LCC round and
   the LCC fixpoint (Alg. 4/5), one NLCC constraint (Alg. 6/7, as an injective
   rooted-embedding search), final template-driven search with match counting
-  (Remark 1, Section 4.7).
+  (Remark 1, Section 4.7), and the listing of every match with per-vertex and
+  per-entry participation counts (the analyses of the Introduction).
 * `constraints.py` -- non-local constraint generation (Table 3, Alg. 2).
 * `pipeline.py`    -- the main loop (Alg. 1) over the pieces above.
 """
@@ -22,23 +23,44 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ccpm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle in place with gcc -O2 (no OpenMP, one thread)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    """Compile the C oracle in place with gcc -O2: liboracle.so runs on one
+    thread (the pragmas are ignored), liboracle_omp.so with OpenMP runs the
+    loops the source marks as independent on every host core."""
+    for path, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wno-unknown-pragmas"] + extra +
+                                  ["-o", tmp, _SRC])
+            os.replace(tmp, path)
     return _LIB
 
 
+def threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else every core)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env else (os.cpu_count() or 1)
+
+
+_parallel = False
+
+
+def set_parallel(on: bool) -> None:
+    """Route every oracle call through the OpenMP build (True) or the
+    single-threaded one (False, the default).  Results are identical."""
+    global _parallel
+    _parallel = bool(on)
+
+
 def lib():
-    global _lib
-    if _lib is None:
+    key = "omp" if _parallel else "serial"
+    if key not in _libs:
         build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(_LIB_OMP if _parallel else _LIB)
         i64, i32, u32p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
         vp = ctypes.c_void_p
         L.oracle_init.argtypes = [i64, vp, vp, vp, i32, vp, vp, vp]
@@ -51,8 +73,10 @@ def lib():
         L.oracle_nlcc.restype = ctypes.c_int
         L.oracle_final.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, vp]
         L.oracle_final.restype = ctypes.c_int
-        _lib = L
-    return _lib
+        L.oracle_matches.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, ctypes.c_uint64, vp, vp]
+        L.oracle_matches.restype = ctypes.c_uint64
+        _libs[key] = L
+    return _libs[key]
 
 
 def _p(a: np.ndarray):
@@ -143,6 +167,20 @@ def final(g: Graph, labels, edges, omega, A, cap: int, with_scanned=False):
     if with_scanned:
         return int(st), om2, A2, int(cnt[0]), int(ns[0])
     return int(st), om2, A2, int(cnt[0])
+
+
+def matches(g: Graph, labels, edges, omega, A, list_cap: int = 0):
+    """Every match inside (omega, A): (count, list [min(count, list_cap), n0]
+    int32, per-vertex counts uint64 [n], per-entry counts uint64 [m])."""
+    _, tadj = template_tables(labels, edges)
+    n0 = len(labels)
+    te = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lst = np.zeros((max(list_cap, 1), n0), dtype=np.int32)
+    vc = np.zeros(max(g.n, 1), dtype=np.uint64)
+    ec = np.zeros(max(g.m, 1), dtype=np.uint64)
+    cnt = lib().oracle_matches(g.n, _p(g.rp), _p(g.col), n0, _p(tadj), len(edges), _p(te),
+                               _p(omega), _p(A), _p(lst), int(list_cap), _p(vc), _p(ec))
+    return int(cnt), lst[: min(int(cnt), list_cap)], vc[: g.n], ec[: g.m]
 
 
 def pack_bits(A: np.ndarray) -> np.ndarray:

@@ -91,6 +91,10 @@ int oracle_lcc_round(int64_t n, const int64_t *rp, const int32_t *col,
                      uint32_t *om_out, uint8_t *A_out, int64_t *scanned)
 {
     int changed = 0;
+    int64_t sc = 0;
+    /* every v writes only om_out[v]: the vertices can be processed in any
+     * order, or in parallel when built with OpenMP */
+#pragma omp parallel for schedule(dynamic, 4096) reduction(|:changed) reduction(+:sc)
     for (int64_t v = 0; v < n; v++) {
         uint32_t wv = om_in[v];
         if (wv == 0) { om_out[v] = 0; continue; }
@@ -98,7 +102,7 @@ int oracle_lcc_round(int64_t n, const int64_t *rp, const int32_t *col,
         int64_t n_alive_edges = 0;
         for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
             if (!A_in[e]) continue;
-            *scanned += 1;
+            sc += 1;
             uint32_t wu = om_in[col[e]];
             if (!compatible(n0, tadj, wv, wu)) continue;
             omega_prime |= wu;
@@ -130,6 +134,9 @@ int oracle_lcc_round(int64_t n, const int64_t *rp, const int32_t *col,
         om_out[v] = keep;
         if (keep != wv) changed = 1;
     }
+    *scanned += sc;
+    /* every v writes only the entries of its own row */
+#pragma omp parallel for schedule(dynamic, 4096) reduction(|:changed)
     for (int64_t v = 0; v < n; v++) {
         for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
             int64_t u = col[e];
@@ -193,6 +200,12 @@ typedef struct {
     const int32_t *e0;     /* template edges, 2 per edge (enumeration marking) */
     uint32_t *om_mark;
     uint8_t *A_mark;
+    /* listing (oracle_matches only) */
+    int32_t *list;         /* row c = phi of the c-th match found, template id order */
+    uint64_t list_cap;
+    int n0;
+    uint64_t *vcnt;        /* per vertex: matches that contain it */
+    uint64_t *ecnt;        /* per CSR entry: matches that map a template edge onto it */
 } search_t;
 
 /* BFS over S from `root`, neighbours taken in increasing template id. */
@@ -237,6 +250,18 @@ static int extend(search_t *s, int i)
 {
     if (i == s->k) {
         if (!s->enumerate) return 1;
+        if (s->enumerate == 2) {
+            if (s->list && s->count < s->list_cap)
+                for (int q = 0; q < s->n0; q++) s->list[s->count * (uint64_t)s->n0 + (uint64_t)q] = (int32_t)s->psi[q];
+            s->count++;
+            for (int q = 0; q < s->n0; q++) s->vcnt[s->psi[q]] += 1;
+            for (int t = 0; t < s->n_e0; t++) {
+                int64_t x = s->psi[s->e0[2 * t]], y = s->psi[s->e0[2 * t + 1]];
+                s->ecnt[entry_of(s->rp, s->col, x, y)] += 1;
+                s->ecnt[entry_of(s->rp, s->col, y, x)] += 1;
+            }
+            return 0;
+        }
         s->count++;
         for (int j = 0; j < s->k; j++) {
             int q = s->order[j];
@@ -295,22 +320,32 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
     if (!om0 || !A0) { free(om0); free(A0); return -1; }
     memcpy(om0, omega, sizeof(uint32_t) * (size_t)n);
     memcpy(A0, A, (size_t)m);
-    search_t s;
-    memset(&s, 0, sizeof(s));
-    s.n = n; s.rp = rp; s.col = col; s.omega = om0; s.A = A0;
-    for (int q = 0; q < 32; q++) s.sadj[q] = sadj[q] & svert;
+    search_t s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.n = n; s0.rp = rp; s0.col = col; s0.omega = om0; s0.A = A0;
+    for (int q = 0; q < 32; q++) s0.sadj[q] = sadj[q] & svert;
+    int64_t tokens = 0, scanned = 0;
     for (int h = 0; h < 32; h++) {
         if (!((heads >> h) & 1u) || !((svert >> h) & 1u)) continue;
-        make_order(&s, svert, h);
-        for (int64_t v = 0; v < n; v++) {
-            if (!((om0[v] >> h) & 1u)) continue;
-            *n_tokens += 1;
-            for (int j = 0; j < 32; j++) s.psi[j] = -1;
-            s.psi[h] = v;
-            int sat = extend(&s, 1);
-            if (!sat) omega[v] &= ~(1u << h);
+        make_order(&s0, svert, h);
+        /* every issuer is searched against the snapshot and writes only its
+         * own omega word: issuers are independent */
+#pragma omp parallel reduction(+:tokens, scanned)
+        {
+            search_t s = s0;
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t v = 0; v < n; v++) {
+                if (!((om0[v] >> h) & 1u)) continue;
+                tokens += 1;
+                for (int j = 0; j < 32; j++) s.psi[j] = -1;
+                s.psi[h] = v;
+                int sat = extend(&s, 1);
+                if (!sat) omega[v] &= ~(1u << h);
+            }
+            scanned += s.scanned;
         }
     }
+    *n_tokens += tokens;
     int changed = 0;
     for (int64_t v = 0; v < n; v++) {
         if (omega[v] != om0[v]) changed = 1;
@@ -322,7 +357,7 @@ int oracle_nlcc(int64_t n, const int64_t *rp, const int32_t *col,
             }
         }
     }
-    *n_scanned += s.scanned;
+    *n_scanned += scanned;
     free(om0);
     free(A0);
     return changed;
@@ -371,34 +406,94 @@ int oracle_final(int64_t n, const int64_t *rp, const int32_t *col,
     memset(om_out, 0, sizeof(uint32_t) * (size_t)n);
     memset(A_out, 0, (size_t)m);
     s.enumerate = 0;
+    int64_t scanned = s.scanned;
+    /* existence searches are independent of each other: per (v, q) the only
+     * write is om_out[v]; per entry the writes set flags to 1 (atomically,
+     * as a reverse entry belongs to another row) */
     for (int q = 0; q < n0; q++) {
         make_order(&s, all, q);
-        for (int64_t v = 0; v < n; v++) {
-            if (!((omega[v] >> q) & 1u)) continue;
-            for (int j = 0; j < 32; j++) s.psi[j] = -1;
-            s.psi[q] = v;
-            if (extend(&s, 1)) om_out[v] |= 1u << q;
+#pragma omp parallel reduction(+:scanned)
+        {
+            search_t t = s;
+            t.scanned = 0;
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t v = 0; v < n; v++) {
+                if (!((omega[v] >> q) & 1u)) continue;
+                for (int j = 0; j < 32; j++) t.psi[j] = -1;
+                t.psi[q] = v;
+                if (extend(&t, 1)) om_out[v] |= 1u << q;
+            }
+            scanned += t.scanned;
         }
     }
-    for (int t = 0; t < m0; t++) {
-        int a = tedges[2 * t], b = tedges[2 * t + 1];
+    for (int te = 0; te < m0; te++) {
+        int a = tedges[2 * te], b = tedges[2 * te + 1];
         make_order_edge(&s, all, a, b);
-        for (int64_t x = 0; x < n; x++) {
-            if (!((omega[x] >> a) & 1u)) continue;
-            for (int64_t e = rp[x]; e < rp[x + 1]; e++) {
-                int64_t y = col[e];
-                if (!A[e] || !((omega[y] >> b) & 1u) || A_out[e]) continue;
-                for (int j = 0; j < 32; j++) s.psi[j] = -1;
-                s.psi[a] = x;
-                s.psi[b] = y;
-                if (extend(&s, 2)) {
-                    A_out[e] = 1;
-                    A_out[entry_of(rp, col, y, x)] = 1;
+#pragma omp parallel reduction(+:scanned)
+        {
+            search_t t = s;
+            t.scanned = 0;
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t x = 0; x < n; x++) {
+                if (!((omega[x] >> a) & 1u)) continue;
+                for (int64_t e = rp[x]; e < rp[x + 1]; e++) {
+                    int64_t y = col[e];
+                    uint8_t done;
+#pragma omp atomic read
+                    done = A_out[e];
+                    if (!A[e] || !((omega[y] >> b) & 1u) || done) continue;
+                    for (int j = 0; j < 32; j++) t.psi[j] = -1;
+                    t.psi[a] = x;
+                    t.psi[b] = y;
+                    if (extend(&t, 2)) {
+                        int64_t r = entry_of(rp, col, y, x);
+#pragma omp atomic write
+                        A_out[e] = 1;
+#pragma omp atomic write
+                        A_out[r] = 1;
+                    }
                 }
             }
+            scanned += t.scanned;
         }
     }
     *count = 0;
-    *n_scanned += s.scanned;
+    *n_scanned += scanned;
     return OR_EBUDGET;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Every match of the template inside (omega, A), for the analyses the paper  */
+/* names as the point of pruning (Introduction: listing the matches, and     */
+/* per-vertex / per-edge participation, i.e. match-based centrality).  Plain */
+/* backtracking from template vertex 0 over vertices in increasing id; a      */
+/* match phi is listed as phi(0..n0-1) (the first list_cap of them, in the    */
+/* order found).  vcnt[v] = number of matches with v in phi(V0); ecnt[e] =    */
+/* number of matches that map a template edge onto the undirected edge of     */
+/* entry e (both entries of an edge get the same count).  Returns the number  */
+/* of matches.                                                               */
+/* ------------------------------------------------------------------------ */
+uint64_t oracle_matches(int64_t n, const int64_t *rp, const int32_t *col,
+                        int n0, const uint32_t *tadj, int m0, const int32_t *tedges,
+                        const uint32_t *omega, const uint8_t *A,
+                        int32_t *list, uint64_t list_cap, uint64_t *vcnt, uint64_t *ecnt)
+{
+    int64_t m = rp[n];
+    memset(vcnt, 0, sizeof(uint64_t) * (size_t)n);
+    memset(ecnt, 0, sizeof(uint64_t) * (size_t)m);
+    search_t s;
+    memset(&s, 0, sizeof(s));
+    s.n = n; s.rp = rp; s.col = col; s.omega = omega; s.A = A;
+    s.enumerate = 2; s.cap = (uint64_t)-1; s.n_e0 = m0; s.e0 = tedges;
+    s.list = list; s.list_cap = list_cap; s.n0 = n0; s.vcnt = vcnt; s.ecnt = ecnt;
+    uint32_t all = (n0 >= 32) ? 0xFFFFFFFFu : ((1u << n0) - 1u);
+    for (int q = 0; q < n0; q++) s.sadj[q] = tadj[q];
+    make_order(&s, all, 0);
+    for (int64_t v = 0; v < n; v++) {
+        if (!(omega[v] & 1u)) continue;
+        for (int j = 0; j < 32; j++) s.psi[j] = -1;
+        s.psi[0] = v;
+        extend(&s, 1);
+    }
+    return s.count;
 }

@@ -55,7 +55,10 @@ class Counts(ctypes.Structure):
                 ("lcc_alg_bytes", ctypes.c_int64), ("lcc_row_entries", ctypes.c_int64),
                 ("lcc_active_vertices", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("lcc_compactions", ctypes.c_int64), ("ms_search_kernel", ctypes.c_double),
-                ("search_launches", ctypes.c_int64), ("search_entries_nlcc", ctypes.c_int64)]
+                ("search_launches", ctypes.c_int64), ("search_entries_nlcc", ctypes.c_int64),
+                ("lcc_kernel_bytes", ctypes.c_int64), ("lcc_first_entries", ctypes.c_int64),
+                ("ms_lcc_first", ctypes.c_double), ("ms_final_count", ctypes.c_double),
+                ("ms_final_vertex", ctypes.c_double), ("ms_final_edge", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +74,16 @@ class ConstraintLog(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["features"] = list(self.features)
         return d
+
+
+class ExploreVariant(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("removed", ctypes.c_uint64),
+                ("active_v", ctypes.c_int64), ("active_e_dir", ctypes.c_int64),
+                ("match_embeddings", ctypes.c_uint64), ("count_valid", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ConstraintInfo(ctypes.Structure):
@@ -115,6 +128,10 @@ def _load():
         "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
         "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
         "ccpm_graph_batch_workers": ([vp], i32),
+        "ccpm_result_matches": ([vp, vp, vp, P(Options), vp, ctypes.c_uint64, vp, vp, i32,
+                                 P(ctypes.c_uint64)], i32),
+        "ccpm_explore": ([vp, vp, vp, i32, P(Options), P(ExploreVariant), i32, P(i32), P(i32),
+                          P(ctypes.c_double), P(vp)], i32),
         "ccpm_state_export": ([vp, vp, P(ctypes.c_size_t)], i32),
         "ccpm_state_import": ([vp, vp, vp, vp, ctypes.c_size_t, P(vp)], i32),
         "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
@@ -138,7 +155,7 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc",
             "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
             "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train",
-            "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers"]
+            "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers", "ccpm_result_matches", "ccpm_explore"]
 
 
 def _ptr(a):
@@ -319,6 +336,31 @@ class Result:
         """Generated-order indices of the constraints, in the order they ran."""
         return [r["constraint"] for r in self.logs()]
 
+    def matches(self, tmpl, list_cap: int = 0, vertex_counts: bool = False, entry_counts: bool = False,
+                opts=None, device: bool = False):
+        """ccpm_result_matches: (n_matches, list [min(n, list_cap), n0] int32,
+        per-vertex counts uint64 [n] or None, per-entry counts uint64 [m] or
+        None).  device=True returns CUDA tensors filled in place."""
+        n0 = len(tmpl.labels)
+        g = self.graph
+        if device:
+            import torch
+            dev = torch.device("cuda", g.ctx.device)
+            lst = torch.zeros((max(list_cap, 1), n0), dtype=torch.int32, device=dev)
+            vc = torch.zeros(g.n, dtype=torch.int64, device=dev) if vertex_counts else None
+            ec = torch.zeros(max(g.m, 1), dtype=torch.int64, device=dev) if entry_counts else None
+        else:
+            lst = np.zeros((max(list_cap, 1), n0), dtype=np.int32)
+            vc = np.zeros(g.n, dtype=np.uint64) if vertex_counts else None
+            ec = np.zeros(max(g.m, 1), dtype=np.uint64) if entry_counts else None
+        nm = ctypes.c_uint64(0)
+        p = lambda x: _ptr(x)[0] if x is not None else None
+        rc = lib.ccpm_result_matches(g.ctx.h, self.h, tmpl.h, ctypes.byref(opts) if opts is not None else None,
+                                     p(lst), int(list_cap), p(vc), p(ec), int(device), ctypes.byref(nm))
+        g.ctx.check(rc, "ccpm_result_matches")
+        k = min(int(nm.value), list_cap)
+        return int(nm.value), lst[:k], vc, (ec[: g.m] if ec is not None else None)
+
     def export_state(self) -> bytes:
         """ccpm_state_export: the state as one self-describing byte blob."""
         n = ctypes.c_size_t(0)
@@ -368,11 +410,27 @@ def lcc_fixpoint_noalloc(device, row_ptr, col, labels, tmpl_labels, tmpl_edges, 
     the library, for callers that cannot allocate device memory while they
     run.  Graph arrays and the omega / ebits outputs are CUDA tensors the
     caller owns.  Returns (rounds, edges_scanned)."""
+    import torch
     tl = np.ascontiguousarray(np.asarray(tmpl_labels, dtype=np.uint8))
     te = np.ascontiguousarray(np.asarray(tmpl_edges, dtype=np.int32).reshape(-1))
+    arrays = {"row_ptr": row_ptr, "col": col, "labels": labels, "omega": omega, "ebits": ebits}
+    for name, x in arrays.items():
+        if not isinstance(x, torch.Tensor) or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous torch tensor")
+    n = int(row_ptr.numel()) - 1
+    m = int(col.numel())
+    want = {"row_ptr": ((torch.int64,), n + 1), "col": ((torch.int32,), m), "labels": ((torch.uint8,), n),
+            "omega": ((torch.int32, torch.uint32), n), "ebits": ((torch.int32, torch.uint32), (m + 31) // 32)}
+    for name, (dtypes, need) in want.items():
+        x = arrays[name]
+        if x.dtype not in dtypes:
+            raise ValueError(f"{name} must have dtype {' or '.join(str(d) for d in dtypes)}, not {x.dtype}")
+        if x.numel() < need:
+            raise ValueError(f"{name} holds {x.numel()} elements, needs at least {need}")
+    for name, x in arrays.items():
+        if not x.is_cuda or x.device.index != int(device):
+            raise ValueError(f"{name} must be a tensor on cuda:{int(device)}, not {x.device}")
     ptrs = [_ptr(x) for x in (row_ptr, col, labels, omega, ebits)]
-    if not all(dev for _, dev in ptrs):
-        raise ValueError("graph arrays and outputs must be device tensors")
     rounds = ctypes.c_int32()
     scanned = ctypes.c_int64()
     err = ctypes.create_string_buffer(256)
@@ -384,6 +442,22 @@ def lcc_fixpoint_noalloc(device, row_ptr, col, labels, tmpl_labels, tmpl_edges, 
     if rc:
         raise CcpmError(rc, f"ccpm_lcc_fixpoint_noalloc: {err.value.decode()}")
     return rounds.value, scanned.value
+
+
+def explore(ctx: Context, graph: Graph, base: Template, max_removed: int, opts: Options | None = None,
+            allow_budget: bool = False, variants_cap: int = 4096):
+    """ccpm_explore: (level found or -1, union Result, per-variant records,
+    milliseconds spent building the candidate set)."""
+    recs = (ExploreVariant * max(variants_cap, 1))()
+    nv, lvl, msc = ctypes.c_int32(0), ctypes.c_int32(-1), ctypes.c_double(0.0)
+    h = ctypes.c_void_p()
+    rc = lib.ccpm_explore(ctx.h, graph.h, base.h, int(max_removed), ctypes.byref(opts) if opts is not None else None,
+                          recs, int(variants_cap), ctypes.byref(nv), ctypes.byref(lvl), ctypes.byref(msc),
+                          ctypes.byref(h))
+    if rc and not (rc == CCPM_EBUDGET and allow_budget):
+        ctx.check(rc, "ccpm_explore")
+    out = [recs[i].as_dict() for i in range(min(nv.value, variants_cap))]
+    return lvl.value, Result(graph, h), out, msc.value
 
 
 def prune_batch(ctx: Context, graph: Graph, tmpls, opts: Options | None = None, results=None,

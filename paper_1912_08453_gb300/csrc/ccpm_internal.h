@@ -12,7 +12,7 @@ namespace ccpm {
 
 constexpr int kMaxT = 32;           // template vertices (omega is one uint32)
 constexpr int kMaxCls = 32;         // label-multiplicity classes per template
-constexpr int kSmallDeg = 32;       // rows up to this length: 4 lanes per vertex
+constexpr int kSmallDeg = 64;       // rows up to this length: the flat short-row path
 constexpr int kDefaultHubDeg = 1024;// longer rows are split into chunks of this size
 constexpr int kMaxHubDeg = 1 << 24; // larger hub_degree options are clamped to this
 constexpr uint64_t kDefaultSearchBudget = 1ull << 22;

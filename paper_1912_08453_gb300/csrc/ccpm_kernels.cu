@@ -82,6 +82,13 @@ struct SmemTmpl {
     int n_cls;
 };
 
+// Per warp: the rows of one batch of the short-row path.
+struct ShortRows {
+    int64_t off[32];      // row i's entry k of the batch stream is CSR entry off[i] + k
+    uint32_t nbr[32];     // template neighbours of omega(v_i)
+    int row[32];          // row whose piece of the current step starts at this lane
+};
+
 __device__ __forceinline__ void load_tmpl(SmemTmpl &s, const DevTmpl &t) {
     for (int i = threadIdx.x; i < kMaxT; i += blockDim.x) s.adj[i] = t.adj[i];
     for (int i = threadIdx.x; i < kMaxCls; i += blockDim.x) {
@@ -238,7 +245,12 @@ struct LccArgs {
     int hub_deg;
     int64_t *deg;                 // entries each listed vertex keeps (0 if it dies), or nullptr
     int med_chunk;                // medium vertices a warp prefetches together (1..16)
-    int small_chunk;              // short-row vertices a warp prefetches together (8, 16 or 32)
+    int small_chunk;              // unused by the short-row path (32 rows per batch)
+    // first round after a fresh init: omega(u) is the initial mask of u's
+    // label, so the neighbour gather reads the 1-byte label instead of the
+    // 4-byte omega word (lab0 = labels, lmask = label -> initial omega)
+    const uint8_t *lab0;
+    LabelMask lmask;
 };
 
 template <int MAXC>
@@ -270,7 +282,8 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const int32_t *__restrict__ col,
                                               const uint32_t *__restrict__ om, uint32_t *ebits,
                                               const SmemTmpl &s, Partial<MAXC> &p,
-                                              uint32_t &scanned) {
+                                              uint32_t &scanned, const uint8_t *__restrict__ lab0,
+                                              const uint32_t *slm) {
     constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
     const int64_t w0 = beg >> 5;
@@ -296,7 +309,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
         for (int j = 0; j < UNR; j++) {
             const int rel = rel0 + j * 32;
             act[j] = rel >= lo && rel < hi && ((word[j] >> lane) & 1u);
-            u[j] = act[j] ? __ldg(c0 + j * 32) : 0;
+            u[j] = act[j] ? __ldcs(c0 + j * 32) : 0;
         }
     };
     load_step(0);
@@ -306,7 +319,8 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             was[j] = act[j];
-            wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+            if (lab0) wu[j] = act[j] ? slm[__ldg(lab0 + u[j])] : 0u;
+            else wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
         }
         if (k0 + UNR < nwin) load_step(k0 + UNR);
 #pragma unroll
@@ -345,58 +359,6 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
     }
 }
 
-// Group form for rows of at most 32 entries: G lanes share a row; failing
-// entries, and those whose other end is inactive, are collected as a
-// row-relative mask and cleared once per row.
-template <int G, int MAXC, bool DENSE>
-__device__ __forceinline__ uint32_t scan_row_group(int64_t beg, int64_t end, uint32_t nbr_v, int lane_g,
-                                                   const int32_t *__restrict__ col,
-                                                   const uint32_t *__restrict__ om, const uint32_t *ebits,
-                                                   const SmemTmpl &s, Partial<MAXC> &p,
-                                                   uint32_t &scanned) {
-    constexpr int UNR = 32 / G;   // covers the whole row in one pass
-    uint32_t word[UNR];
-    int32_t u[UNR];
-    bool act[UNR];
-#pragma unroll
-    for (int j = 0; j < UNR; j++) {
-        const int64_t e = beg + lane_g + j * G;
-        word[j] = DENSE ? ~0u : 0u;
-        if (!DENSE && e < end) word[j] = ebits[e >> 5];
-    }
-#pragma unroll
-    for (int j = 0; j < UNR; j++) {
-        const int64_t e = beg + lane_g + j * G;
-        act[j] = (e < end) && ((word[j] >> (uint32_t)(e & 31)) & 1u);
-        u[j] = act[j] ? __ldg(col + e) : 0;
-    }
-    uint32_t wu[UNR];
-#pragma unroll
-    for (int j = 0; j < UNR; j++) wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
-    uint32_t clr = 0u;
-#pragma unroll
-    for (int j = 0; j < UNR; j++) {
-        const uint32_t w = wu[j];
-        if (!w) {
-            // other end already inactive: drop the bit (no change of the state)
-            if (act[j]) clr |= 1u << (uint32_t)(lane_g + j * G);
-            continue;
-        }
-        scanned++;
-        if (w & nbr_v) {
-            p.U |= w;
-            p.nN++;
-#pragma unroll
-            for (int c = 0; c < MAXC; c++)
-                if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
-        } else {
-            p.achg = 1u;
-            clr |= 1u << (uint32_t)(lane_g + j * G);
-        }
-    }
-    return clr;
-}
-
 // Clear the entries of a row (at most 32 long) given by a row-relative mask.
 __device__ __forceinline__ void clear_rel(uint32_t *ebits, int64_t beg, uint32_t clr) {
     if (!clr) return;
@@ -428,14 +390,165 @@ __device__ __forceinline__ uint32_t nbr_mask(uint32_t wv, const SmemTmpl &s) {
     return m;
 }
 
+// Round counters one warp accumulates (summed once at the end of the kernel).
+struct LccTally {
+    uint32_t scanned = 0;          // per lane
+    unsigned long long rows = 0, alive = 0, kept = 0, rows_next = 0;   // lane 0 (or the row lanes)
+    uint32_t changed = 0;
+};
+
+// Short rows, 32 per warp batch (lane i owns row i of the batch).  The rows'
+// entries are walked as one stream, 32 per step with one entry per lane, so
+// lanes stay busy whatever the row lengths.  A step holds pieces of several
+// rows: every lane finds its row from the piece starts, and per-row sums are
+// segmented warp reductions whose result each row's lane collects.  The
+// column loads stream past the caches (read once per round).
+template <int MAXC, bool DENSE>
+__device__ __forceinline__ void short_rows_batch(const LccArgs &a, const SmemTmpl &s, const uint32_t *slm,
+                                                 ShortRows &sr, int64_t idx0, WarpBuf<int32_t> &bs,
+                                                 LccTally &tl) {
+    const int lane = (int)lane_id();
+    const int64_t idx = idx0 + lane;
+    int32_t v = -1;
+    uint32_t wv = 0u;
+    int64_t b = 0;
+    int d = 0;
+    if (idx < a.n_small) {
+        v = a.small_in[idx];
+        wv = __ldg(a.om_cur + v);
+        if (wv) {
+            b = a.rp[v];
+            d = (int)(a.rp[v + 1] - b);
+        }
+    }
+    const uint32_t nbr = wv ? nbr_mask(wv, s) : 0u;
+    int S = d;                                   // inclusive prefix of the row lengths
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL_MASK, S, o);
+        if (lane >= o) S += t;
+    }
+    const int T = __shfl_sync(FULL_MASK, S, 31);
+    const int start = S - d;
+    sr.off[lane] = b - start;
+    sr.nbr[lane] = nbr;
+    uint32_t U = 0u, N = 0u;
+    uint32_t cnt[MAXC > 0 ? MAXC : 1];
+#pragma unroll
+    for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) cnt[c] = 0u;
+    __syncwarp();
+    for (int k0 = 0; k0 < T; k0 += 32) {
+        // the piece of row `lane` inside this step: lanes [lo, hi)
+        const int lo = max(start, k0) - k0, hi = min(start + d, k0 + 32) - k0;
+        const bool ov = lo < hi;
+        if (ov) sr.row[lo] = lane;
+        const uint32_t H = __reduce_or_sync(FULL_MASK, ov ? (1u << lo) : 0u);   // piece starts (bit 0 always)
+        __syncwarp();
+        const uint32_t upto = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
+        const int seg_lo = 31 - __clz(H & upto);
+        const uint32_t above = H & ~upto;
+        const int seg_hi = above ? __ffs(above) - 1 : 32;
+        const uint32_t seg = (seg_hi == 32 ? FULL_MASK : ((1u << seg_hi) - 1u)) & ~((1u << seg_lo) - 1u);
+        const int r = sr.row[seg_lo];
+        const int k = k0 + lane;
+        const bool valid = k < T;
+        const int64_t e = sr.off[r] + k;
+        const uint32_t nb = sr.nbr[r];
+        bool act = valid;
+        if (!DENSE && valid) act = (__ldg(a.ebits + (e >> 5)) >> (uint32_t)(e & 31)) & 1u;
+        uint32_t w = 0u;
+        if (act) {
+            const int32_t u = __ldcs(a.col + e);
+            w = a.lab0 ? slm[__ldg(a.lab0 + u)] : __ldg(a.om_cur + u);
+        }
+        const bool keep = (w & nb) != 0u;
+        tl.scanned += w != 0u;
+        if (w != 0u && !keep) tl.changed = 1u;           // eta eliminates a live entry
+        // entries whose other end is already inactive lose their bit too (no
+        // change of the state: such an entry is inactive already)
+        const uint32_t dm = __ballot_sync(FULL_MASK, act && !keep) & seg;
+        uint32_t ru, gk[MAXC > 4 ? MAXC : 1];
+        uint32_t rk;
+        ru = __reduce_or_sync(seg, keep ? w : 0u);
+        if constexpr (MAXC <= 4) {
+            // the kept count and up to four class counts of a piece (each at
+            // most 32) packed in 6-bit fields
+            uint32_t pk = keep ? 1u : 0u;
+#pragma unroll
+            for (int c = 0; c < MAXC; c++)
+                if (keep && c < s.n_cls && (w & s.cls_mask[c])) pk += 1u << (6 * (c + 1));
+            rk = __reduce_add_sync(seg, pk);
+        } else {
+            rk = __reduce_add_sync(seg, keep ? 1u : 0u);
+#pragma unroll
+            for (int c = 0; c < MAXC; c++)
+                gk[c] = c < s.n_cls ? __reduce_add_sync(seg, (keep && (w & s.cls_mask[c])) ? 1u : 0u) : 0u;
+        }
+        if (lane == seg_lo && dm) {
+            // the piece's entries are consecutive from e: at most two words
+            const uint32_t bits = dm >> seg_lo;
+            const uint32_t sh = (uint32_t)(e & 31);
+            atomicAnd(&a.ebits[e >> 5], ~(bits << sh));
+            if (sh && (bits >> (32 - sh))) atomicAnd(&a.ebits[(e >> 5) + 1], ~(bits >> (32 - sh)));
+        }
+        // each row's lane takes the sums of its piece
+        const int src = ov ? lo : 0;
+        const uint32_t gu = __shfl_sync(FULL_MASK, ru, src);
+        const uint32_t gr = __shfl_sync(FULL_MASK, rk, src);
+        if constexpr (MAXC <= 4) {
+            if (ov) {
+                U |= gu;
+                N += gr & 63u;
+#pragma unroll
+                for (int c = 0; c < MAXC; c++) cnt[c] += (gr >> (6 * (c + 1))) & 63u;
+            }
+        } else {
+            uint32_t gc[MAXC];
+#pragma unroll
+            for (int c = 0; c < MAXC; c++) gc[c] = __shfl_sync(FULL_MASK, gk[c], src);
+            if (ov) {
+                U |= gu;
+                N += gr;
+#pragma unroll
+                for (int c = 0; c < MAXC; c++) cnt[c] += gc[c];
+            }
+        }
+        __syncwarp();                            // sr.row is rewritten by the next step
+    }
+    if (v >= 0) {
+        uint32_t keep = 0u;
+        if (wv) {
+            Partial<MAXC> p;
+            p.U = U;
+            p.nN = N;
+#pragma unroll
+            for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) p.cnt[c] = cnt[c];
+            keep = decide<MAXC>(wv, p, s);
+            tl.rows += (unsigned long long)d;
+            tl.alive++;
+            if (keep) { tl.kept += N; tl.rows_next += (unsigned long long)d; }
+            if (keep != wv) tl.changed = 1u;
+            if (keep == 0u) clear_row<1>(a.ebits, b, b + d, 0);
+        }
+        a.om_next[v] = keep;
+        if (a.deg) a.deg[v] = keep ? (int64_t)N : 0;
+    }
+    // the batch's vertices that were active at the start of the round
+    bs.push(v >= 0 && wv != 0u, v);
+}
+
 template <int MAXC, bool DENSE>
 __global__ void __launch_bounds__(256, 4)
 k_lcc_round(LccArgs a, DevTmpl t) {
     __shared__ SmemTmpl s;
+    __shared__ uint32_t slm[256];
     __shared__ int32_t sbuf[2][8][32];
     __shared__ ChunkItem cbuf[8][32];
+    __shared__ ShortRows srows[8];
     __shared__ int scnt[3][8];
     load_tmpl(s, t);
+    if (a.lab0)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) slm[i] = a.lmask.m[i];
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     if (lane == 0) { scnt[0][wib] = 0; scnt[1][wib] = 0; scnt[2][wib] = 0; }
@@ -445,9 +558,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     WarpBuf<ChunkItem> bc{cbuf[wib], &scnt[2][wib], a.chunk_out, &a.st->n_chunk};
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t scanned = 0;          // per lane: at most one entry per window
-    unsigned long long rows = 0, alive = 0, kept = 0, rows_next = 0;
-    uint32_t changed = 0;
+    LccTally tl;
 
     // (1) pieces of long rows: one warp per piece, combined through HubAcc;
     // the last piece to finish decides for the vertex.
@@ -464,9 +575,10 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         const int64_t rbeg = a.rp[ci.v], rend = a.rp[ci.v + 1];
         const int64_t beg = rbeg + (int64_t)ci.c * a.hub_deg;
         const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
-        if (lane == 0) { rows += (unsigned long long)(end - beg); alive += ci.c == 0; }
+        if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
-        scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
+        scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
+                                   slm);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -498,8 +610,8 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 a.om_next[ci.v] = keep;
                 if (a.deg) a.deg[ci.v] = keep ? (int64_t)tot.nN : 0;
             }
-            if (lane == 0 && keep) { kept += tot.nN; rows_next += (unsigned long long)(rend - rbeg); }
-            if (keep != wv || tot.achg) changed = 1u;
+            if (lane == 0 && keep) { tl.kept += tot.nN; tl.rows_next += (unsigned long long)(rend - rbeg); }
+            if (keep != wv || tot.achg) tl.changed = 1u;
             if (keep == 0u) clear_row<32>(a.ebits, rbeg, rend, lane);
             __syncwarp();
             if (lane == 0) {
@@ -532,9 +644,10 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             const int64_t beg = __shfl_sync(FULL_MASK, bl, j), end = __shfl_sync(FULL_MASK, el, j);
             uint32_t keep = 0u, p_nN = 0u;
             if (wv) {
-                if (lane == 0) { rows += (unsigned long long)(end - beg); alive++; }
+                if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
-                scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, scanned);
+                scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned,
+                                           a.lab0, slm);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
                 p.achg = grp_or<32>(p.achg);
@@ -542,8 +655,8 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<32>(p.cnt[c]);
                 keep = decide<MAXC>(wv, p, s);
                 p_nN = p.nN;
-                if (lane == 0 && keep) { kept += p.nN; rows_next += (unsigned long long)(end - beg); }
-                if (keep != wv || p.achg) changed = 1u;
+                if (lane == 0 && keep) { tl.kept += p.nN; tl.rows_next += (unsigned long long)(end - beg); }
+                if (keep != wv || p.achg) tl.changed = 1u;
                 if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
             }
             if (lane == 0) {
@@ -555,69 +668,31 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         bm.push(vl >= 0 && wl != 0u, vl);
     }
 
-    // (3) short rows: 4 lanes per vertex, 8 vertices per warp step; the list
-    // entries, omega and row offsets of 32 vertices are loaded at once
-    const int g = lane >> 2, lg = lane & 3;
-    const int SB = a.small_chunk;
-    const int64_t n_schunks = (a.n_small + SB - 1) / SB;
-    for (int64_t ch = gwarp; ch < n_schunks; ch += nwarps) {
-        const int64_t idx = ch * SB + lane;
-        int32_t vl = -1;
-        uint32_t wl = 0u;
-        int64_t bl = 0, el = 0;
-        if (lane < SB && idx < a.n_small) {
-            vl = a.small_in[idx];
-            wl = __ldg(a.om_cur + vl);
-            if (wl) { bl = a.rp[vl]; el = a.rp[vl + 1]; }
-        }
-        for (int step = 0; step < SB / 8; step++) {
-            const int src = step * 8 + g;
-            const int32_t v = __shfl_sync(FULL_MASK, vl, src);
-            const uint32_t wv = __shfl_sync(FULL_MASK, wl, src);
-            const int64_t beg = __shfl_sync(FULL_MASK, bl, src), end = __shfl_sync(FULL_MASK, el, src);
-            if (lg == 0 && wv) { rows += (unsigned long long)(end - beg); alive++; }
-            Partial<MAXC> p;
-            uint32_t clr = scan_row_group<4, MAXC, DENSE>(beg, end, nbr_mask(wv, s), lg, a.col, a.om_cur, a.ebits,
-                                                          s, p, scanned);
-            clr = grp_or<4>(clr);
-            p.achg = grp_or<4>(p.achg);
-            if (lg == 0 && wv) clear_rel(a.ebits, beg, clr);
-            p.U = grp_or<4>(p.U);
-            p.nN = grp_sum<4>(p.nN);
-#pragma unroll
-            for (int c = 0; c < MAXC; c++) p.cnt[c] = grp_sum<4>(p.cnt[c]);
-            uint32_t keep = wv ? decide<MAXC>(wv, p, s) : 0u;
-            if (lg == 0 && keep) { kept += p.nN; rows_next += (unsigned long long)(end - beg); }
-            if (wv && (keep != wv || p.achg)) changed = 1u;
-            if (wv && keep == 0u) clear_row<4>(a.ebits, beg, end, lg);
-            if (v >= 0 && lg == 0) {
-                a.om_next[v] = keep;
-                if (a.deg) a.deg[v] = keep ? (int64_t)p.nN : 0;
-            }
-        }
-        bs.push(vl >= 0 && wl != 0u, vl);
-    }
+    // (3) short rows: 32 vertices per warp batch, entries streamed flat
+    const int64_t n_sbatch = (a.n_small + 31) / 32;
+    for (int64_t ch = gwarp; ch < n_sbatch; ch += nwarps)
+        short_rows_batch<MAXC, DENSE>(a, s, slm, srows[wib], ch * 32, bs, tl);
 
     bs.flush();
     bm.flush();
     bc.flush();
     // warp totals
-    unsigned long long scanned64 = scanned;
+    unsigned long long scanned64 = tl.scanned;
     for (int o = 16; o > 0; o >>= 1) {
         scanned64 += __shfl_xor_sync(FULL_MASK, scanned64, o);
-        rows += __shfl_xor_sync(FULL_MASK, rows, o);
-        alive += __shfl_xor_sync(FULL_MASK, alive, o);
-        kept += __shfl_xor_sync(FULL_MASK, kept, o);
-        rows_next += __shfl_xor_sync(FULL_MASK, rows_next, o);
-        changed |= __shfl_xor_sync(FULL_MASK, changed, o);
+        tl.rows += __shfl_xor_sync(FULL_MASK, tl.rows, o);
+        tl.alive += __shfl_xor_sync(FULL_MASK, tl.alive, o);
+        tl.kept += __shfl_xor_sync(FULL_MASK, tl.kept, o);
+        tl.rows_next += __shfl_xor_sync(FULL_MASK, tl.rows_next, o);
+        tl.changed |= __shfl_xor_sync(FULL_MASK, tl.changed, o);
     }
     if (lane == 0) {
         if (scanned64) atomicAdd(&a.st->scanned, scanned64);
-        if (rows) atomicAdd(&a.st->row_entries, rows);
-        if (alive) atomicAdd(&a.st->alive, alive);
-        if (kept) atomicAdd(&a.st->kept, kept);
-        if (rows_next) atomicAdd(&a.st->rows_next, rows_next);
-        if (changed) atomicOr(&a.st->changed, 1u);
+        if (tl.rows) atomicAdd(&a.st->row_entries, tl.rows);
+        if (tl.alive) atomicAdd(&a.st->alive, tl.alive);
+        if (tl.kept) atomicAdd(&a.st->kept, tl.kept);
+        if (tl.rows_next) atomicAdd(&a.st->rows_next, tl.rows_next);
+        if (tl.changed) atomicOr(&a.st->changed, 1u);
     }
 }
 
@@ -1020,6 +1095,16 @@ struct SearchArgs {
     int64_t spill_cap;        // untried candidates on here as new items (0: never)
     uint64_t spill_after;
     int enum_heads;           // k_expand: 1 = final search (one head), 0 = NLCC
+    const uint32_t *sat_seed; // existence passes: heads already known satisfied (nullable)
+    // listing (mode kList): every match found gets an index from list_count;
+    // the first list_cap are written as n0 vertex ids in template order; vcnt
+    // and ecnt (nullable) count the matches per vertex and per CSR entry
+    int32_t *list_out;
+    uint64_t list_cap;
+    int list_n0;
+    unsigned long long *list_count;
+    unsigned long long *vcnt;
+    unsigned long long *ecnt;
 };
 
 constexpr int kMaxBack = 4;  // joins per level whose label group is kept in shared memory
@@ -1157,6 +1242,29 @@ __device__ __forceinline__ void mark_edges(const SearchArgs &a, const DevPlan &P
     __syncwarp();
 }
 
+// A match found by a listing search: stored (if its index is below the cap)
+// and counted on every vertex and on both entries of every edge it uses.
+__device__ __forceinline__ void list_embedding(const SearchArgs &a, const DevPlan &P, const WarpSearch &W) {
+    const int lane = (int)lane_id();
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(a.list_count, 1ull);
+    idx = __shfl_sync(FULL_MASK, idx, 0);
+    if (lane < P.k) {
+        const int32_t x = W.psi[lane];
+        if (idx < a.list_cap) a.list_out[idx * (unsigned long long)a.list_n0 + (unsigned long long)P.q[lane]] = x;
+        if (a.vcnt) atomicAdd(&a.vcnt[x], 1ull);
+    }
+    if (a.ecnt) {
+        for (int t = lane; t < P.n_marks; t += 32) {
+            const int32_t x = W.psi[P.mark_a[t]], y = W.psi[P.mark_b[t]];
+            const int64_t e1 = find_entry(a.rp, a.col, x, y), e2 = find_entry(a.rp, a.col, y, x);
+            if (e1 >= 0) atomicAdd(&a.ecnt[e1], 1ull);
+            if (e2 >= 0) atomicAdd(&a.ecnt[e2], 1ull);
+        }
+    }
+    __syncwarp();
+}
+
 // Is the entry e of the scanned label group a valid image u for position d?
 // Its omega must hold q_d, it must differ from earlier same-label images, and
 // it must be joined to every other placed neighbour of position d.
@@ -1221,8 +1329,8 @@ __device__ __forceinline__ void mark_vertices(const SearchArgs &a, const DevPlan
 }
 
 // Search modes: does an embedding exist / count the embeddings / count them
-// and mark the vertices and edges of every one.
-constexpr int kExist = 0, kCount = 1, kMark = 2;
+// and mark the vertices and edges of every one / count them and list them.
+constexpr int kExist = 0, kCount = 1, kMark = 2, kList = 3;
 
 // Hand the rest of a long search to other warps: for every open level L
 // (d0..d) each untried candidate c -- the remaining bits of the level's
@@ -1303,6 +1411,7 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
         if (MODE == kExist) return true;
         matches++;
         if (MODE == kMark) { mark_vertices(a, P, W); mark_edges(a, P, W); }
+        if (MODE == kList) list_embedding(a, P, W);
         return false;
     }
     open_level(a, P, W, d0);
@@ -1351,9 +1460,13 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
         __syncwarp();
         if (d == k - 1) {
             if (MODE == kExist) return true;
-            matches++;                              // kMark (counting never stores last-level masks)
-            mark_vertices(a, P, W);
-            mark_edges(a, P, W);
+            matches++;                              // kMark / kList (counting never stores last-level masks)
+            if (MODE == kList) {
+                list_embedding(a, P, W);
+            } else {
+                mark_vertices(a, P, W);
+                mark_edges(a, P, W);
+            }
             continue;
         }
         d++;
@@ -1378,8 +1491,9 @@ k_nlcc_search(SearchArgs a) {
     bool over = false;
     for (int64_t it = grab_root(a); it < a.n_roots; it = grab_root(a)) {
         const int32_t v = a.roots[it];
-        const uint32_t hv = __ldg(a.om + v) & a.heads;
-        uint32_t sat = 0;
+        const uint32_t seed = a.sat_seed ? __ldg(a.sat_seed + v) : 0u;
+        const uint32_t hv = __ldg(a.om + v) & a.heads & ~seed;
+        uint32_t sat = seed;
         for (uint32_t hm = hv; hm; hm &= hm - 1u) {
             const int h = __ffs(hm) - 1;
             if (lane == 0) { W.psi[0] = v; W.done_word = nullptr; }
@@ -1446,8 +1560,9 @@ k_expand(SearchArgs a) {
     unsigned long long entries = 0, tokens = 0;
     for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
         const int32_t v = a.roots[it];
-        const uint32_t hv = a.enum_heads ? a.heads : (__ldg(a.om + v) & a.heads);
-        if (!a.enum_heads && lane == 0) a.sat[v] = 0u;
+        const uint32_t seed = (!a.enum_heads && a.sat_seed) ? __ldg(a.sat_seed + v) : 0u;
+        const uint32_t hv = a.enum_heads ? a.heads : (__ldg(a.om + v) & a.heads & ~seed);
+        if (!a.enum_heads && lane == 0) a.sat[v] = seed;
         tokens += (unsigned long long)__popc(hv);
         for (uint32_t hm = hv; hm; hm &= hm - 1u) {
             const int h = __ffs(hm) - 1;
@@ -1655,10 +1770,9 @@ k_edge_items(SearchArgs a, EdgeTab tab) {
             for (int o = 0; o < tab.n; o++) {
                 const bool ok = wy && ((wx >> tab.a[o]) & 1u) && ((wy >> tab.b[o]) & 1u);
                 SearchItem si;
+                for (int j = 0; j < kItemMaxDepth; j++) si.psi[j] = 0;
                 si.psi[0] = x;
                 si.psi[1] = y;
-                si.psi[5] = (int32_t)(e >> 32);
-                si.psi[6] = (int32_t)(e & 0xFFFFFFFF);
                 si.hd = o | (2 << 8);
                 b.push(ok, si);
             }
@@ -1679,17 +1793,21 @@ k_edge_search(SearchArgs a) {
         const int64_t it1 = min(a.n_items, it0 + kItemBatch);
         for (int64_t it = it0; it < it1; it++) {
             const SearchItem item = a.items[it];
-            const int o = item.hd & 0xff;
-            const int64_t e = ((int64_t)(uint32_t)item.psi[5] << 32) | (int64_t)(uint32_t)item.psi[6];
+            const int o = item.hd & 0xff, depth = item.hd >> 8;
+            // the entry of the item's template edge: psi[0], psi[1] are its
+            // ends (items handed on by long searches keep them)
+            int64_t e = 0;
+            if (lane == 0) e = find_entry(a.rp, a.col, item.psi[0], item.psi[1]);
+            e = __shfl_sync(FULL_MASK, e, 0);
             uint32_t done = 0;                          // marked by an embedding found meanwhile?
             if (lane == 0) done = (*(volatile uint32_t *)&a.eb_out[e >> 5] >> (uint32_t)(e & 31)) & 1u;
             if (__shfl_sync(FULL_MASK, done, 0)) continue;
-            if (lane < 2) W.psi[lane] = item.psi[lane];
-            if (lane == 0) { W.done_word = &a.eb_out[e >> 5]; W.done_bit = 1u << (uint32_t)(e & 31); }
+            if (lane < depth) W.psi[lane] = item.psi[lane];
+            if (lane == 0) { W.done_word = &a.eb_out[e >> 5]; W.done_bit = 1u << (uint32_t)(e & 31); W.head = o; }
             __syncwarp();
             const DevPlan &P = a.plans[o];
             bool ran_out = false;
-            if (search_from<kExist>(a, P, 2, W, entries, matches, ran_out)) {
+            if (search_from<kExist>(a, P, depth, W, entries, matches, ran_out)) {
                 if (!ran_out) {
                     mark_edges(a, P, W);
                 } else if (lane == 0) {
@@ -2122,7 +2240,8 @@ constexpr uint64_t kSpillAfter = 2048;
 // Run an item kernel, then again over the items long searches handed on, until
 // none are left (each round of items is strictly deeper, so at most one pass
 // per template position).  kind 0: NLCC existence (k_nlcc_items), 1: final
-// count, 2: final count and mark.  Counting (and marking) stops once the cap
+// count, 2: final count and mark, 3: count and list, 4: per-entry existence
+// (k_edge_search).  Counting (and marking) stops once the cap
 // is passed.
 int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t split, int64_t &launches,
                 int64_t &passes) {
@@ -2143,7 +2262,9 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t s
         passes++;
         if (kind == 0) k_nlcc_items<<<gi, 128, 0, s>>>(a);
         else if (kind == 1) k_final_items<kCount><<<gi, 128, 0, s>>>(a);
-        else k_final_items<kMark><<<gi, 128, 0, s>>>(a);
+        else if (kind == 2) k_final_items<kMark><<<gi, 128, 0, s>>>(a);
+        else if (kind == 3) k_final_items<kList><<<gi, 128, 0, s>>>(a);
+        else k_edge_search<<<gi, 128, 0, s>>>(a);
         CU(ctx, cudaGetLastError());
         CU(ctx, cudaMemcpyAsync(&w.aux_h[1], &w.st->n_spill, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaMemcpyAsync(&w.aux_h[2], &w.st->overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -2152,7 +2273,7 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t s
         const unsigned int spilled = std::min((unsigned int)(w.aux_h[1] & 0xFFFFFFFFull),
                                               (unsigned int)(w.aux_h[3] & 0xFFFFFFFFull));
         const unsigned int over = (unsigned int)(w.aux_h[2] & 0xFFFFFFFFull);
-        if (spilled == 0 || (kind != 0 && over)) break;
+        if (spilled == 0 || (kind != 0 && kind != 4 && over)) break;
         a.n_items = spilled;
         cur ^= 1;
     }
@@ -2200,11 +2321,15 @@ struct Pipeline {
     DevTmpl dt;
     int cur = 0;            // omega buffer holding round-k state
     bool dense = true;      // next round is the first after init: all edge bits set
+    bool from_labels = false;  // next round is the first after a fresh init: omega = initial label mask
+    LabelMask lm0{};        // label -> initial omega (Alg. 3)
     int li = 0;             // frontier list parity
     int64_t n_small = 0, n_med = 0, n_chunk = 0;
     int64_t scanned = 0;
     int64_t windows = 0;
     int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
+    int64_t alg_bytes = 0, kernel_bytes = 0, first_entries = 0;
+    double ms_first = 0.0;
     double ms_lcc_kernel = 0.0;
     double ms_search_kernel = 0.0;
     int64_t search_launches = 0, nlcc_entries = 0, item_passes = 0;
@@ -2265,6 +2390,9 @@ struct Pipeline {
         a.st = w.st;
         a.hub_deg = w.hub_deg;
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
+        a.lab0 = from_labels ? g->lab : nullptr;
+        a.lmask = lm0;
+        from_labels = false;
         // prefetch units: large enough to hide the per-vertex loads, small
         // enough that every resident warp gets several of them
         const int64_t resident = (int64_t)ctx->num_sms * 32;
@@ -2308,6 +2436,13 @@ struct Pipeline {
             scanned += (int64_t)w.st_h->scanned;
             rows += (int64_t)w.st_h->row_entries;
             alive += (int64_t)w.st_h->alive;
+            alg_bytes += (33 * (int64_t)w.st_h->scanned) / 4 + 16 * (int64_t)w.st_h->alive;
+            kernel_bytes += 24 * (int64_t)w.st_h->alive + (33 * (int64_t)w.st_h->row_entries) / 8 +
+                            4 * (int64_t)w.st_h->scanned;
+            if (lcc_launches == 1) {
+                first_entries = (int64_t)w.st_h->scanned;
+                ms_first = ms;
+            }
             n_small = w.st_h->n_small;
             n_med = w.st_h->n_med;
             n_chunk = w.st_h->n_chunk;
@@ -2783,6 +2918,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     LabelMask lm;
     std::memset(&lm, 0, sizeof(lm));
     for (int q = 0; q < t.n0; q++) lm.m[t.labels[q]] |= 1u << q;
+    P.lm0 = lm;
+    P.from_labels = !resume;
     if (resume) {
         // a saved state: its edge bits, then (below) its omega inside the initial one
         CUF(cudaMemcpyAsync(w.ebits, r->eb, sizeof(uint32_t) * (size_t)w.words, cudaMemcpyDeviceToDevice, s));
@@ -2865,13 +3002,15 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                 pick = first_noop;
             } else {
                 // the network predicts -log2(1 + microseconds) of running each
-                // constraint now; a constraint k places later in the fixed order
-                // runs first only if it is predicted more than 2^k times cheaper
+                // constraint now; a later constraint of the fixed order runs
+                // first if it is predicted more than twice as cheap as the fixed
+                // order's next one (the one predicted cheapest among those), so
+                // expensive checks wait for a state that cheaper ones have shrunk
                 std::vector<float> score(remaining.size());
                 P.launches++;
                 RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
                 for (size_t i = 1; i < remaining.size(); i++)
-                    if (score[i] - (float)i > score[pick] - (float)pick) pick = i;
+                    if (score[i] > score[0] + 1.f && score[i] > score[pick]) pick = i;
             }
         }
         const bool noop = is_noop(pick);
@@ -2991,6 +3130,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     bool count_valid = false;
     uint64_t matches = 0;
     bool final_done = false;
+    float ms_fc = 0.f, ms_fv = 0.f, ms_fe = 0.f;
+    cudaEvent_t fev[4] = {w.ev[6], w.ev[7], w.ev[8], w.ev[9]};
     if (opt.run_final) {
         const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
         if (P.want_compact(true) || P.cheaper_than_label_rows()) RCF(P.compact());
@@ -3014,17 +3155,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         a.items = w.items;
         a.items_cap = w.items_cap;
         auto run_items = [&](bool edge_pass) -> int {
-            if (!edge_pass) {
-                int rc2 = item_passes(ctx, w, a, 0, split, P.launches, P.item_passes);
-                return rc2 ? rc2 : P.read_stats();
-            }
-            // edge items keep the entry index in their last two slots: not split further
-            CU(ctx, cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
-            P.launches++;
-            const int gi = grid_for(ctx, (a.n_items + kItemBatch - 1) / kItemBatch * 32, 128, 16);
-            k_edge_search<<<gi, 128, 0, s>>>(a);
-            CU(ctx, cudaGetLastError());
-            return P.read_stats();
+            int rc2 = item_passes(ctx, w, a, edge_pass ? 4 : 0, split, P.launches, P.item_passes);
+            return rc2 ? rc2 : P.read_stats();
         };
         // the final enumeration keeps the background label frequencies (measured
         // faster than ordering by live candidates there)
@@ -3088,6 +3220,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         // kMarkCap matches, one more enumeration marks them, and past that the
         // existence passes answer omega* and E*.
         bool capped = false;
+        CUF(cudaEventRecord(fev[0], s));
         RCF(count_pass(kMark, w.om[P.cur], std::min<uint64_t>(opt.max_embeddings, kFewMatches), matches, capped));
         if (!capped) {
             count_valid = true;
@@ -3105,11 +3238,14 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         } else {
             count_valid = false;
         }
+        CUF(cudaEventRecord(fev[1], s));
         if (!final_done) {
-            CUF(cudaMemsetAsync(r->om, 0, sizeof(uint32_t) * (size_t)g->n, s));
-            CUF(cudaMemsetAsync(r->eb, 0, sizeof(uint32_t) * (size_t)(w.words + 1), s));
+            // the capped enumeration's marks stay: every one belongs to a match
+            // found, so the existence searches below skip those (vertex,
+            // template vertex) pairs and entries
             a.om_out = nullptr;
             a.eb_out = r->eb;
+            a.sat_seed = r->om;
         }
         if (!final_done) {
             // (A) every (v, q): some match has phi(q) = v?  Found embeddings also
@@ -3149,6 +3285,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                 k_sat_to_omega<<<grid_for(ctx, n_roots, 256, 8), 256, 0, s>>>(w.roots, n_roots, w.sat, w.om[P.cur], r->om);
                 CUF(cudaGetLastError());
             }
+            a.sat_seed = nullptr;
+            CUF(cudaEventRecord(fev[2], s));
             // (B) every entry between omega* vertices that no embedding has marked
             // yet: some match maps a template edge onto it?
             std::vector<std::pair<int, int>> oriented;
@@ -3171,23 +3309,45 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                     build_plan(t, all, t.adj, tab.a[o], g->label_freq, true, w.plans_h[o], tab.b[o], live);
                 }
                 CUF(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan) * (size_t)tab.n, cudaMemcpyHostToDevice, s));
-                CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
                 a.om = r->om;
-                a.n_roots = n_roots;
-                P.launches++;
-                k_edge_items<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a, tab);
-                CUF(cudaGetLastError());
-                RCF(P.read_stats());
-                a.n_items = w.st_h->n_items;
-                if (a.n_items > w.items_cap)
-                    return fail(set_err(ctx, CCPM_EOVERFLOW, "edge pass: too many candidate edges"));
-                if (a.n_items > 0) {
-                    RCF(run_items(true));
-                    if (w.st_h->overflow) over = true;
-                    P.windows += (int64_t)w.st_h->windows;
+                // the candidate entries of a range of roots become items; a range
+                // whose items do not fit is halved and made again (the bits marked
+                // so far stay: every one of them is a found match's edge)
+                int64_t span = n_roots;
+                for (int64_t r0 = 0; r0 < n_roots;) {
+                    const int64_t r1 = std::min(n_roots, r0 + span);
+                    CUF(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+                    a.roots = w.roots + r0;
+                    a.n_roots = r1 - r0;
+                    P.launches++;
+                    k_edge_items<<<grid_for(ctx, a.n_roots * 32, 256, 8), 256, 0, s>>>(a, tab);
+                    CUF(cudaGetLastError());
+                    RCF(P.read_stats());
+                    a.n_items = w.st_h->n_items;
+                    if (a.n_items > w.items_cap) {
+                        if (r1 - r0 == 1)
+                            return fail(set_err(ctx, CCPM_EOVERFLOW, "edge pass: one vertex has too many candidate edges"));
+                        span = std::max<int64_t>(1, (r1 - r0) / 2);
+                        continue;
+                    }
+                    if (a.n_items > 0) {
+                        RCF(run_items(true));
+                        if (w.st_h->overflow) over = true;
+                        P.windows += (int64_t)w.st_h->windows;
+                    }
+                    r0 = r1;
                 }
+                a.roots = w.roots;
+                a.n_roots = n_roots;
             }
+            CUF(cudaEventRecord(fev[3], s));
+            CUF(cudaStreamSynchronize(s));
+            cudaEventElapsedTime(&ms_fv, fev[1], fev[2]);
+            cudaEventElapsedTime(&ms_fe, fev[2], fev[3]);
+        } else {
+            CUF(cudaStreamSynchronize(s));
         }
+        cudaEventElapsedTime(&ms_fc, fev[0], fev[1]);
         final_done = true;
     }
     if (!final_done) {
@@ -3232,7 +3392,13 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     cn.ms_lcc_kernel = P.ms_lcc_kernel;
     cn.lcc_row_entries = P.rows;
     cn.lcc_active_vertices = P.alive;
-    cn.lcc_alg_bytes = 24 * P.alive + 4 * P.rows + P.rows / 8 + 4 * P.scanned;
+    cn.lcc_alg_bytes = P.alg_bytes;
+    cn.lcc_kernel_bytes = P.kernel_bytes;
+    cn.lcc_first_entries = P.first_entries;
+    cn.ms_lcc_first = P.ms_first;
+    cn.ms_final_count = ms_fc;
+    cn.ms_final_vertex = ms_fv;
+    cn.ms_final_edge = ms_fe;
     cn.kernel_launches = P.launches;
     cn.lcc_compactions = P.compactions;
     cn.ms_search_kernel = P.ms_search_kernel;
@@ -3343,6 +3509,194 @@ int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *t
     return CCPM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+__global__ void k_or_words(uint32_t *dst, const uint32_t *src, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] |= src[i];
+}
+
+// A result on graph g for template t holding (om, eb) copied from `src`
+// arrays (the candidate set), ready for a resumed prune.
+int result_from(ccpm_ctx *ctx, ccpm_graph *g, const Template &t, const uint32_t *om, const uint32_t *eb,
+                int64_t words, ccpm_result **out) {
+    ccpm_result *r = new (std::nothrow) ccpm_result();
+    if (!r) return set_err(ctx, CCPM_ENOMEM, "result: host allocation");
+    r->g = g;
+    int rc;
+    if ((rc = dalloc(ctx, &r->om, (size_t)g->n)) || (rc = dalloc(ctx, &r->eb, (size_t)words + 1))) {
+        cudaFree(r->om); cudaFree(r->eb);
+        delete r;
+        return rc;
+    }
+    r->tmpl_fp = tmpl_fingerprint(t);
+    cudaError_t e = cudaMemcpyAsync(r->om, om, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->eb, eb, sizeof(uint32_t) * (size_t)(words + 1), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(r->om); cudaFree(r->eb);
+        delete r;
+        return set_err(ctx, CCPM_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
+    }
+    *out = r;
+    return CCPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccpm_explore(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t base, int max_removed, const ccpm_options *opt_in,
+                 ccpm_explore_variant *variants, int variants_cap, int *n_variants, int *level_found,
+                 double *ms_candidates, ccpm_result_t *out) {
+    if (!ctx || !g || !base || !out || max_removed < 0 || (variants_cap > 0 && !variants)) return CCPM_EINVAL;
+    if (g->ctx->device != ctx->device) return set_err(ctx, CCPM_EINVAL, "graph lives on another device");
+    const Template &B = base->t;
+    const int m0 = (int)B.edges.size();
+    if (m0 > 64) return set_err(ctx, CCPM_EINVAL, "explore: the base template may have at most 64 edges");
+    ccpm_options opt;
+    if (opt_in) opt = *opt_in; else ccpm_options_default(&opt);
+    opt.resume = 0;
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (n_variants) *n_variants = 0;
+    if (level_found) *level_found = -1;
+    if (ms_candidates) *ms_candidates = 0.0;
+    cudaStream_t s = ctx->stream;
+    const int64_t words = (g->m + 31) / 32;
+    // connected variants by level: every set of `k` template edges whose
+    // removal leaves the template connected (vertices are never removed, so
+    // template vertex q means the same in every variant)
+    struct Variant { int level; uint64_t removed; Template t; };
+    std::vector<Variant> vs;
+    for (int k = 0; k <= std::min(max_removed, m0 - 1); k++) {
+        std::vector<int> pick(k);
+        for (int i = 0; i < k; i++) pick[i] = i;
+        for (;;) {
+            uint64_t mask = 0;
+            for (int i : pick) mask |= 1ull << i;
+            std::vector<int32_t> ed;
+            for (int e = 0; e < m0; e++)
+                if (!((mask >> e) & 1ull)) { ed.push_back(B.edges[(size_t)e].first); ed.push_back(B.edges[(size_t)e].second); }
+            Variant v{k, mask, Template{}};
+            if (template_build(v.t, B.n0, B.labels, (int)ed.size() / 2, ed.data()) == CCPM_OK) vs.push_back(std::move(v));
+            int i = k - 1;
+            while (i >= 0 && pick[(size_t)i] == m0 - k + i) i--;
+            if (i < 0) break;
+            pick[(size_t)i]++;
+            for (int j = i + 1; j < k; j++) pick[(size_t)j] = pick[(size_t)j - 1] + 1;
+        }
+    }
+    // the candidate set: the union of the LCC fixpoints of every variant (local
+    // constraints only, so each costs one LCC to fixpoint); it holds every
+    // match of every variant
+    uint32_t *c_om = nullptr, *c_eb = nullptr;
+    int rc;
+    if ((rc = dalloc(ctx, &c_om, (size_t)g->n)) || (rc = dalloc(ctx, &c_eb, (size_t)words + 1))) {
+        cudaFree(c_om); cudaFree(c_eb);
+        return rc;
+    }
+    auto cleanup = [&]() { cudaFree(c_om); cudaFree(c_eb); };
+    auto fail_c = [&](int code) { cleanup(); return code; };
+    cudaEvent_t e0 = ctx->ws.ev[0], e1 = ctx->ws.ev[1];
+    if (cudaMemsetAsync(c_om, 0, sizeof(uint32_t) * (size_t)g->n, s) != cudaSuccess ||
+        cudaMemsetAsync(c_eb, 0, sizeof(uint32_t) * (size_t)(words + 1), s) != cudaSuccess)
+        return fail_c(set_err(ctx, CCPM_ECUDA, "explore: memset"));
+    ccpm_options lcc_only = opt;
+    lcc_only.run_final = 0;
+    lcc_only.order_mode = CCPM_ORDER_FIXED;
+    auto t_start = std::chrono::steady_clock::now();
+    for (auto &v : vs) {
+        ccpm_tmpl tl;
+        tl.ctx = ctx;
+        tl.t = v.t;
+        tl.t.generated = true;          // no non-local constraint: LCC only
+        tl.t.k0.clear();
+        tl.t.order.clear();
+        ccpm_result *r = nullptr;
+        rc = ccpm_prune(ctx, g, &tl, &lcc_only, &r);
+        if (rc && rc != CCPM_EBUDGET) return fail_c(rc);
+        const int gr = grid_for(ctx, std::max<int64_t>(g->n, words), 256, 8);
+        k_or_words<<<gr, 256, 0, s>>>(c_om, r->om, g->n);
+        k_or_words<<<gr, 256, 0, s>>>(c_eb, r->eb, words);
+        ccpm_result_destroy(r);
+        if (cudaGetLastError() != cudaSuccess) return fail_c(set_err(ctx, CCPM_ECUDA, "explore: union"));
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail_c(set_err(ctx, CCPM_ECUDA, "explore: sync"));
+    if (ms_candidates)
+        *ms_candidates = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    // the union of the matching variants' omega* and E* at the first level
+    // with a match
+    ccpm_result *u = *out;
+    if (u && u->g != g) return fail_c(set_err(ctx, CCPM_EINVAL, "explore: result was made for another graph"));
+    if (!u) {
+        if ((rc = result_from(ctx, g, B, c_om, c_eb, words, &u))) return fail_c(rc);
+    }
+    u->tmpl_fp = tmpl_fingerprint(B);
+    u->phase_rounds.clear();
+    u->logs.clear();
+    std::memset(&u->counts, 0, sizeof(u->counts));
+    cudaMemsetAsync(u->om, 0, sizeof(uint32_t) * (size_t)g->n, s);
+    cudaMemsetAsync(u->eb, 0, sizeof(uint32_t) * (size_t)(words + 1), s);
+    int found = -1, nv = 0;
+    bool budget = false;
+    ccpm_options resumed = opt;
+    resumed.resume = 1;
+    for (int k = 0; k <= max_removed && found < 0; k++) {
+        bool any = false;
+        for (auto &v : vs) {
+            if (v.level != k) continue;
+            ccpm_tmpl tv;
+            tv.ctx = ctx;
+            tv.t = v.t;
+            ccpm_result *r = nullptr;
+            if ((rc = result_from(ctx, g, tv.t, c_om, c_eb, words, &r))) return fail_c(rc);
+            rc = ccpm_prune(ctx, g, &tv, &resumed, &r);
+            if (rc == CCPM_EBUDGET) budget = true;
+            else if (rc) { ccpm_result_destroy(r); return fail_c(rc); }
+            const ccpm_counts &c = r->counts;
+            if (c.active_v > 0) {
+                any = true;
+                const int gr = grid_for(ctx, std::max<int64_t>(g->n, words), 256, 8);
+                k_or_words<<<gr, 256, 0, s>>>(u->om, r->om, g->n);
+                k_or_words<<<gr, 256, 0, s>>>(u->eb, r->eb, words);
+            }
+            if (nv < variants_cap) {
+                ccpm_explore_variant &o = variants[nv];
+                o.level = k;
+                o.n_edges = (int32_t)v.t.edges.size();
+                o.removed = v.removed;
+                o.active_v = c.active_v;
+                o.active_e_dir = c.active_e_dir;
+                o.match_embeddings = c.match_embeddings;
+                o.count_valid = c.count_valid;
+                o.status = c.status;
+                o.ms_total = c.ms_total;
+            }
+            nv++;
+            ccpm_result_destroy(r);
+        }
+        if (any) found = k;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail_c(set_err(ctx, CCPM_ECUDA, "explore: sync"));
+    cleanup();
+    (void)e0; (void)e1;
+    if (n_variants) *n_variants = nv;
+    if (level_found) *level_found = found;
+    *out = u;
+    // counts of the union
+    CU(ctx, cudaMemsetAsync(ctx->ws.cnt, 0, 2 * sizeof(unsigned long long), s));
+    k_count<<<grid_for(ctx, std::max<int64_t>(g->n, words), 256, 8), 256, 0, s>>>(g->n, u->om, words, u->eb, ctx->ws.cnt);
+    CU(ctx, cudaGetLastError());
+    CU(ctx, cudaMemcpyAsync(ctx->ws.cnt_h, ctx->ws.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    u->counts.active_v = (int64_t)ctx->ws.cnt_h[0];
+    u->counts.active_e_dir = (int64_t)ctx->ws.cnt_h[1];
+    if (budget) return set_err(ctx, CCPM_EBUDGET, "explore: a search budget was exceeded");
+    return CCPM_OK;
+}
+
 int ccpm_result_omega(ccpm_result_t r, uint32_t *dst, int64_t n, int dst_on_device) {
     if (!r || !dst || n != r->g->n) return CCPM_EINVAL;
     ccpm_ctx *ctx = r->g->ctx;
@@ -3379,6 +3733,129 @@ int ccpm_result_phase_rounds(ccpm_result_t r, int32_t *dst, int cap) {
     if (!r || (!dst && cap > 0)) return CCPM_EINVAL;
     int k = std::min(cap, (int)r->phase_rounds.size());
     for (int i = 0; i < k; i++) dst[i] = r->phase_rounds[(size_t)i];
+    return CCPM_OK;
+}
+
+int ccpm_result_matches(ccpm_ctx_t ctx, ccpm_result_t r, ccpm_tmpl_t tm, const ccpm_options *opt_in,
+                        int32_t *list, uint64_t list_cap, uint64_t *vertex_counts, uint64_t *entry_counts,
+                        int dst_on_device, uint64_t *n_matches) {
+    if (!ctx || !r || !tm || !n_matches || (list_cap > 0 && !list)) return CCPM_EINVAL;
+    *n_matches = 0;
+    ccpm_graph *g = r->g;
+    if (g->ctx->device != ctx->device) return set_err(ctx, CCPM_EINVAL, "result lives on another device");
+    Template &t = tm->t;
+    if (r->tmpl_fp != tmpl_fingerprint(t)) return set_err(ctx, CCPM_EINVAL, "result was made for another template");
+    ccpm_options opt;
+    if (opt_in) opt = *opt_in; else ccpm_options_default(&opt);
+    CU(ctx, cudaSetDevice(ctx->device));
+    const int hub_deg = opt.hub_degree > 0 ? std::min(opt.hub_degree, kMaxHubDeg) : kDefaultHubDeg;
+    const uint64_t budget = opt.search_budget ? opt.search_budget : ~0ull;
+    const uint64_t split = opt.search_split < 0 ? 0 : (opt.search_split == 0 ? kSpillAfter : (uint64_t)opt.search_split);
+    int rc = ws_ensure(ctx, g, hub_deg);
+    if (rc) return rc;
+    if ((rc = ensure_label_rows(ctx, g))) return rc;
+    Workspace &w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    // host outputs are filled through device buffers of this call
+    int32_t *d_list = list;
+    unsigned long long *d_vc = (unsigned long long *)vertex_counts, *d_ec = (unsigned long long *)entry_counts;
+    bool own = false;
+    auto release = [&]() {
+        if (own) { cudaFree(d_list); cudaFree(d_vc); cudaFree(d_ec); }
+    };
+    if (!dst_on_device) {
+        own = true;
+        d_list = nullptr; d_vc = nullptr; d_ec = nullptr;
+        if ((list_cap && (rc = dalloc(ctx, &d_list, (size_t)(list_cap * (uint64_t)t.n0)))) ||
+            (vertex_counts && (rc = dalloc(ctx, &d_vc, (size_t)g->n))) ||
+            (entry_counts && (rc = dalloc(ctx, &d_ec, (size_t)std::max<int64_t>(g->m, 1))))) {
+            release();
+            return rc;
+        }
+    }
+#define CUR(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            release();                                                                   \
+            return set_err(ctx, CCPM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                \
+    } while (0)
+    if (d_vc) CUR(cudaMemsetAsync(d_vc, 0, sizeof(unsigned long long) * (size_t)g->n, s));
+    if (d_ec) CUR(cudaMemsetAsync(d_ec, 0, sizeof(unsigned long long) * (size_t)g->m, s));
+    CUR(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned long long), s));
+    // the root is the template vertex with the rarest label
+    int root = 0;
+    for (int q = 1; q < t.n0; q++)
+        if (g->label_freq[t.labels[q]] < g->label_freq[t.labels[root]]) root = q;
+    const uint32_t all = t.n0 == 32 ? 0xFFFFFFFFu : ((1u << t.n0) - 1u);
+    build_plan(t, all, t.adj, root, g->label_freq, true, w.plans_h[0], -1, nullptr);
+    CUR(cudaMemcpyAsync(w.plans, w.plans_h, sizeof(DevPlan), cudaMemcpyHostToDevice, s));
+    CUR(cudaMemsetAsync(w.st, 0, sizeof(RoundStats), s));
+    k_collect_roots<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, r->om, 1u << root, w.roots, w.st);
+    CUR(cudaGetLastError());
+    CUR(cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, s));
+    CUR(cudaStreamSynchronize(s));
+    const int64_t n_roots = w.st_h->n_roots;
+    bool over = false;
+    if (n_roots > 0) {
+        SearchArgs a{};
+        a.rp = g->rp;
+        a.col = g->col;
+        a.rl = g->rp;
+        a.lcol = g->lcol;
+        a.nlab = g->nlab;
+        a.om = r->om;
+        a.roots = w.roots;
+        a.n_roots = n_roots;
+        a.next_root = w.next_root;
+        a.plans = w.plans;
+        a.heads = 1u << root;
+        a.sat = w.sat;
+        a.st = w.st;
+        a.budget = budget;
+        a.cap = ~0ull;
+        a.items = w.items;
+        a.items_cap = w.items_cap;
+        a.enum_heads = 1;
+        a.list_out = d_list;
+        a.list_cap = list_cap;
+        a.list_n0 = t.n0;
+        a.list_count = w.cnt;
+        a.vcnt = d_vc;
+        a.ecnt = d_ec;
+        int64_t launches = 0, passes = 0;
+        k_expand<<<grid_for(ctx, n_roots * 32, 256, 8), 256, 0, s>>>(a);
+        CUR(cudaGetLastError());
+        CUR(cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, s));
+        CUR(cudaStreamSynchronize(s));
+        a.n_items = w.st_h->n_items;
+        if (a.n_items <= w.items_cap && (rc = expand_more(ctx, w, a, t.n0, launches))) { release(); return rc; }
+        CUR(cudaMemsetAsync(w.next_root, 0, sizeof(unsigned long long), s));
+        if (a.n_items <= w.items_cap) {
+            if ((rc = item_passes(ctx, w, a, 3, split, launches, passes))) { release(); return rc; }
+        } else {
+            k_final_search<kList><<<grid_for(ctx, n_roots * 32, 128, 16), 128, 0, s>>>(a);
+            CUR(cudaGetLastError());
+        }
+        CUR(cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, s));
+        CUR(cudaStreamSynchronize(s));
+        over = w.st_h->overflow != 0;
+    }
+    unsigned long long found = 0;
+    CUR(cudaMemcpyAsync(&found, w.cnt, sizeof(found), cudaMemcpyDeviceToHost, s));
+    CUR(cudaStreamSynchronize(s));
+    if (!dst_on_device) {
+        const uint64_t rows = std::min<uint64_t>((uint64_t)found, list_cap);
+        if (rows) CUR(cudaMemcpyAsync(list, d_list, sizeof(int32_t) * (size_t)(rows * (uint64_t)t.n0), cudaMemcpyDeviceToHost, s));
+        if (d_vc) CUR(cudaMemcpyAsync(vertex_counts, d_vc, sizeof(uint64_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+        if (d_ec) CUR(cudaMemcpyAsync(entry_counts, d_ec, sizeof(uint64_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
+        CUR(cudaStreamSynchronize(s));
+    }
+#undef CUR
+    release();
+    *n_matches = found;
+    if (over) return set_err(ctx, CCPM_EBUDGET, "a listing search ran out of its window budget: outputs incomplete");
     return CCPM_OK;
 }
 
@@ -3604,18 +4081,16 @@ const char *noalloc_template(int n0, const uint8_t *labels, int m0, const int32_
     return nullptr;
 }
 
-}  // namespace
-
-extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t n, int64_t m_dir,
-                                         const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
-                                         int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,
-                                         uint32_t *omega, uint32_t *ebits, int32_t *rounds,
-                                         int64_t *edges_scanned, char *errbuf, size_t errlen) {
+// The body of the entry point below; it may leave another device current.
+int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t m_dir,
+                              const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
+                              int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,
+                              uint32_t *omega, uint32_t *ebits, int32_t *rounds,
+                              int64_t *edges_scanned, char *errbuf, size_t errlen) {
     auto fail = [&](int code, const char *msg) {
         if (errbuf && errlen) std::snprintf(errbuf, errlen, "%s", msg);
         return code;
     };
-    if (errbuf && errlen) errbuf[0] = '\0';
     if (device < 0 || device >= kNoAllocMaxDevices) return fail(CCPM_EINVAL, "device index out of range");
     if (n < 1 || n >= ((int64_t)1 << 31) || m_dir < 0 || !row_ptr || !labels || !omega ||
         (m_dir > 0 && (!col || !ebits)))
@@ -3651,6 +4126,16 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
     e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return fail(CCPM_ECUDA, cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    {
+        // the scratch is sized from m_dir: the offsets must agree with it
+        // before any kernel writes there (two 8-byte reads into the stack)
+        int64_t ends[2] = {-1, -1};
+        e = cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(CCPM_ECUDA, cudaGetErrorString(e));
+        if (ends[0] != 0 || ends[1] != m_dir) return fail(CCPM_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] == m_dir");
+    }
     uint32_t *om[2] = {omega, (uint32_t *)(base + L.om2)};
     int32_t *small[2] = {(int32_t *)(base + L.small[0]), (int32_t *)(base + L.small[1])};
     int32_t *med[2] = {(int32_t *)(base + L.med[0]), (int32_t *)(base + L.med[1])};
@@ -3712,6 +4197,7 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
         a.deg = nullptr;
         a.med_chunk = 1;
         a.small_chunk = 8;
+        a.lab0 = nullptr;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
         if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
         else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);
@@ -3739,4 +4225,21 @@ extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t 
     if (rounds) *rounds = r;
     if (edges_scanned) *edges_scanned = scanned;
     return CCPM_OK;
+}
+
+}  // namespace
+
+// The caller's current device is the same after the call as before it.
+extern "C" int ccpm_lcc_fixpoint_noalloc(int device, void *cuda_stream, int64_t n, int64_t m_dir,
+                                         const int64_t *row_ptr, const int32_t *col, const uint8_t *labels,
+                                         int n0, const uint8_t *tmpl_labels, int m0, const int32_t *tmpl_edges,
+                                         uint32_t *omega, uint32_t *ebits, int32_t *rounds,
+                                         int64_t *edges_scanned, char *errbuf, size_t errlen) {
+    if (errbuf && errlen) errbuf[0] = '\0';
+    int prev = -1;
+    const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+    const int rc = lcc_fixpoint_noalloc_body(device, cuda_stream, n, m_dir, row_ptr, col, labels, n0, tmpl_labels,
+                                             m0, tmpl_edges, omega, ebits, rounds, edges_scanned, errbuf, errlen);
+    if (have_prev && prev != device) cudaSetDevice(prev);
+    return rc;
 }

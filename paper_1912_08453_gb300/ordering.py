@@ -6,9 +6,10 @@ it removed (with its LCC re-run) and its device time.  The network learns
     target = -log2(1 + microseconds spent)
 (optionally plus benefit_weight * log2(1 + bits removed)), i.e. how cheap the
 constraint is to check in that state.  With CCPM_ORDER_LEARNED the pipeline
-keeps the fixed order as a prior: the constraint at position k among the
-remaining ones runs first only if it is predicted more than 2^k times cheaper
-than the fixed order's next one.  Every constraint is still checked, so
+keeps the fixed order as a prior: a later constraint runs first only if it
+is predicted more than twice as cheap as the fixed order's next one (the one
+predicted cheapest among those), so that expensive checks wait for a state
+that cheaper ones have already shrunk.  Every constraint is still checked, so
 omega, the edge bitmap and the match count equal the fixed order's; only the
 order, and with it the LCC round counts and the time, change.
 

@@ -290,3 +290,186 @@ def labels_by_frequency(g: Graph):
     f = label_frequencies(g)
     order = sorted(range(len(f)), key=lambda L: (-f[L], L))
     return [L for L in order if f[L] > 0]
+
+
+# ---------------------------------------------------------------------------
+# Large graphs generated where they are used (scale 20-25)
+#
+# The numpy recipe above draws on one host core; at scales 24-25 (2.7-5.4e8
+# draws of `scale` quadrant choices each) that takes minutes.  The recipe below
+# is the same R-MAT process written as integer torch operations, so it runs on
+# a CUDA device in seconds and gives bit-identical arrays on the CPU (tests
+# check this at small scales).  Its random numbers come from Philox4x32-10
+# (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,
+# 3", SC 2011), a counter-based generator: word j of draw block b of item i is
+# a pure function of (i, stream, b, seed), so chunks can be generated in any
+# order.  Each R-MAT level uses a 16-bit draw (two levels per 32-bit word);
+# the quadrant thresholds are the (A, B, C) cumulative probabilities rounded to
+# multiples of 2^-16.
+# ---------------------------------------------------------------------------
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57      # round multipliers
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85      # Weyl key increments
+_U32 = 0xFFFFFFFF
+
+# Philox streams (third counter word) of the different draws
+_S_EDGE, _S_PERM, _S_LABEL = 1, 2, 3
+
+
+def _mulhilo32(m: int, x):
+    """(hi, lo) 32-bit halves of the 64-bit product m * x, for a constant
+    m < 2^32 and an int64 tensor x of values in [0, 2^32).  The constant is
+    split into 16-bit halves so that no intermediate leaves int64."""
+    mh, ml = m >> 16, m & 0xFFFF
+    a = x * mh                                   # < 2^48
+    b = ((a & 0xFFFF) << 16) + x * ml            # < 2^49
+    return (a >> 16) + (b >> 32), b & _U32
+
+
+def philox4x32(c0, c1, c2, c3, k0: int, k1: int, rounds: int = 10):
+    """Philox4x32-R on int64 tensors holding 32-bit counter words (any shape,
+    broadcast together); key (k0, k1).  Returns the four 32-bit output words
+    as int64 tensors."""
+    import torch
+    x0, x1, x2, x3 = torch.broadcast_tensors(c0, c1, c2, c3)
+    x0, x1, x2, x3 = x0.clone(), x1.clone(), x2.clone(), x3.clone()
+    for r in range(rounds):
+        if r:
+            k0 = (k0 + _PHILOX_W0) & _U32
+            k1 = (k1 + _PHILOX_W1) & _U32
+        hi0, lo0 = _mulhilo32(_PHILOX_M0, x0)
+        hi1, lo1 = _mulhilo32(_PHILOX_M1, x2)
+        x0, x1, x2, x3 = hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0
+    return x0, x1, x2, x3
+
+
+def _draw_words(idx, stream: int, block: int, seed: int):
+    """Four 32-bit Philox words for every item index in `idx` (int64 tensor)."""
+    import torch
+    lo = idx & _U32
+    hi = idx >> 32
+    c2 = torch.full_like(idx, stream)
+    c3 = torch.full_like(idx, block)
+    return philox4x32(lo, hi, c2, c3, seed & _U32, (seed >> 32) & _U32)
+
+
+@dataclasses.dataclass
+class DeviceGraph:
+    """CSR graph held as torch tensors (on any device): row_ptr int64 [n+1],
+    col int32 [m_dir], labels uint8 [n]."""
+    n: int
+    row_ptr: object
+    col: object
+    labels: object
+    name: str = ""
+
+    @property
+    def m_dir(self) -> int:
+        return int(self.col.shape[0])
+
+    def to_host(self) -> Graph:
+        return Graph(self.n, self.row_ptr.cpu().numpy(), self.col.cpu().numpy(),
+                     self.labels.cpu().numpy(), name=self.name)
+
+
+def rmat_edges_philox(scale: int, edge_factor: int = 16, abcd=GRAPH500_ABCD, seed: int = 1,
+                      device="cpu", chunk: int = 1 << 24):
+    """edge_factor * 2^scale directed R-MAT draws (src, dst), int64 tensors on
+    `device`, vertex ids relabelled by a seeded random permutation."""
+    import torch
+    n = 1 << scale
+    m = edge_factor * n
+    t_a = int(round(abcd[0] * 65536))
+    t_ab = int(round((abcd[0] + abcd[1]) * 65536))
+    t_abc = int(round((abcd[0] + abcd[1] + abcd[2]) * 65536))
+    # permutation: stable sort of 64-bit random keys (ties impossible to
+    # matter: a stable sort of equal keys keeps index order)
+    vid = torch.arange(n, dtype=torch.int64, device=device)
+    w = _draw_words(vid, _S_PERM, 0, seed)
+    pkey = (w[0] << 31) | (w[1] >> 1)
+    perm = torch.argsort(pkey, stable=True)
+    del vid, w, pkey
+    srcs, dsts = [], []
+    for lo in range(0, m, chunk):
+        hi = min(m, lo + chunk)
+        idx = torch.arange(lo, hi, dtype=torch.int64, device=device)
+        s = torch.zeros_like(idx)
+        d = torch.zeros_like(idx)
+        words = None
+        for level in range(scale):
+            if level % 8 == 0:
+                words = _draw_words(idx, _S_EDGE, level // 8, seed)
+            wd = words[(level % 8) // 2]
+            r = (wd >> 16) if (level & 1) else (wd & 0xFFFF)
+            sbit = r >= t_ab
+            dbit = ((r >= t_a) & (r < t_ab)) | (r >= t_abc)
+            s |= sbit.to(torch.int64) << level
+            d |= dbit.to(torch.int64) << level
+        srcs.append(perm[s])
+        dsts.append(perm[d])
+        del idx, s, d, words
+    return torch.cat(srcs), torch.cat(dsts)
+
+
+def csr_from_edges_torch(n: int, src, dst):
+    """Symmetrise, drop self loops, deduplicate and sort into CSR (torch, any
+    device); returns (row_ptr int64 [n+1], col int32 [m_dir])."""
+    import torch
+    keep = src != dst
+    s, d = src[keep], dst[keep]
+    del keep
+    keys = torch.cat([s * n + d, d * n + s])
+    del s, d
+    keys = torch.unique(keys, sorted=True)
+    rows = torch.div(keys, n, rounding_mode="floor")
+    col = (keys - rows * n).to(torch.int32)
+    del keys
+    counts = torch.bincount(rows, minlength=n)
+    del rows
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=col.device)
+    torch.cumsum(counts, 0, out=row_ptr[1:])
+    return row_ptr, col
+
+
+def zipf_labels_philox(n: int, n_labels: int = 64, s: float = 1.2, seed: int = 7, device="cpu"):
+    """iid labels with P(k) proportional to (k+1)^-s: a uniform 32-bit Philox
+    word per vertex, looked up in the float64 cumulative distribution."""
+    import torch
+    w = (np.arange(n_labels, dtype=np.float64) + 1.0) ** (-s)
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+    cdf_t = torch.from_numpy(cdf).to(device)
+    vid = torch.arange(n, dtype=torch.int64, device=device)
+    u = _draw_words(vid, _S_LABEL, 0, seed)[0].to(torch.float64) * (1.0 / 4294967296.0)
+    return torch.searchsorted(cdf_t, u, right=True).to(torch.uint8)
+
+
+def degree_labels_torch(row_ptr):
+    """Bit length of every degree (0 for an isolated vertex), uint8."""
+    import torch
+    x = row_ptr[1:] - row_ptr[:-1]
+    lab = torch.zeros(x.shape[0], dtype=torch.uint8, device=x.device)
+    while bool((x > 0).any()):
+        lab += (x > 0).to(torch.uint8)
+        x = x >> 1
+    return lab
+
+
+def rmat_graph_philox(scale: int, edge_factor: int = 16, abcd=GRAPH500_ABCD, seed: int = 1,
+                      labels: str = "zipf", n_labels: int = 64, zipf_s: float = 1.2,
+                      label_seed: int = 7, device="cpu") -> DeviceGraph:
+    """R-MAT graph with the Philox recipe, built on `device` (a CUDA device at
+    scales 20-25; the CPU gives the same arrays, slowly)."""
+    import torch
+    n = 1 << scale
+    with torch.no_grad():
+        src, dst = rmat_edges_philox(scale, edge_factor, abcd, seed, device=device)
+        row_ptr, col = csr_from_edges_torch(n, src, dst)
+        del src, dst
+        if labels == "degree":
+            lab = degree_labels_torch(row_ptr)
+        elif labels == "zipf":
+            lab = zipf_labels_philox(n, n_labels, zipf_s, label_seed, device=device)
+        else:
+            raise ValueError(labels)
+    return DeviceGraph(n, row_ptr, col, lab, name=f"rmat{scale}-{labels}-philox")

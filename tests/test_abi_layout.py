@@ -13,6 +13,7 @@ STRUCTS = {
     "ccpm_counts": "Counts",
     "ccpm_constraint_log": "ConstraintLog",
     "ccpm_constraint_info": "ConstraintInfo",
+    "ccpm_explore_variant": "ExploreVariant",
 }
 
 

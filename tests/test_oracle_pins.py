@@ -489,3 +489,82 @@ def test_lcc_rounds_within_diameter_bound(seed):
     om, A = oracle.init(og, tl, te)
     rounds, _ = oracle.lcc(og, tl, te, om, A)
     assert rounds <= _tree_diameter(n0, te) + 1
+
+
+@pytest.mark.parametrize("L", range(1, 14))
+def test_jacobi_rounds_peel_a_path_one_layer_per_round(L):
+    """Exact round count of snapshot (Jacobi) rounds, computed by hand.
+
+    Triangle template, all labels 0: a template vertex needs two distinct live
+    neighbours.  On a path of L vertices (all label 0) only the two ends lack
+    them; in a snapshot round a vertex sees its neighbours as they were at the
+    start of the round, so round k removes exactly the vertices k-1 steps from
+    an end.  The path is empty after ceil(L/2) rounds and one more round
+    changes nothing: ceil(L/2) + 1 rounds in all.  An in-place (Gauss-Seidel)
+    sweep in index order would empty it in its first round (2 rounds)."""
+    g = wl.graph_from_edge_list(L, [(i, i + 1) for i in range(L - 1)], [0] * L)
+    og = oracle.Graph(g.row_ptr, g.col, g.labels)
+    tl, te = [0, 0, 0], [(0, 1), (1, 2), (0, 2)]
+    om, A = oracle.init(og, tl, te)
+    # round by round: the set removed in round k is {k-1, L-k}
+    alive = set(range(L))
+    for k in range(1, (L + 1) // 2 + 1):
+        ch, om, A, _ = oracle.lcc_round(og, tl, te, om, A)
+        assert ch
+        alive -= {k - 1, L - k}
+        assert set(np.flatnonzero(om).tolist()) == alive, f"round {k}"
+    om, A = oracle.init(og, tl, te)
+    rounds, _ = oracle.lcc(og, tl, te, om, A)
+    assert rounds == (L + 1) // 2 + 1
+    assert not om.any() and not A.any()
+
+
+def test_edge_only_change_counts_a_round():
+    """A round that removes an entry but no omega bit still counts as a
+    change (Alg. 4 sets the change flag for eliminated edges): 2 rounds.
+
+    Template q0 (label 0) - q1 (label 1).  Background: a (0) - b (1) and
+    a (0) - c (0).  Round 1: the entry a-c is not compatible (no template
+    edge joins q0 to q0) and is removed; a keeps q0 through b, b keeps q1,
+    c has no compatible neighbour and dies.  Round 2 changes nothing."""
+    g = wl.graph_from_edge_list(3, [(0, 1), (0, 2)], [0, 1, 0])
+    og = oracle.Graph(g.row_ptr, g.col, g.labels)
+    tl, te = [0, 1], [(0, 1)]
+    om, A = oracle.init(og, tl, te)
+    rounds, _ = oracle.lcc(og, tl, te, om, A)
+    assert rounds == 2
+    assert om.tolist() == [1, 2, 0]
+    # entries of row 0 are (0,1), (0,2); row 1: (1,0); row 2: (2,0)
+    assert A.tolist() == [1, 0, 1, 0]
+    # and with c given label 1 instead, nothing is removed: one quiet round
+    g2 = wl.graph_from_edge_list(3, [(0, 1), (0, 2)], [0, 1, 1])
+    og2 = oracle.Graph(g2.row_ptr, g2.col, g2.labels)
+    om, A = oracle.init(og2, tl, te)
+    rounds, _ = oracle.lcc(og2, tl, te, om, A)
+    assert rounds == 1 and A.all()
+
+
+def test_openmp_build_gives_identical_results():
+    """The OpenMP build of the oracle parallelises only loops whose
+    iterations write disjoint words (or set flags to 1): every output equals
+    the single-threaded build's, including the existence passes past the
+    count cap."""
+    g = wl.rmat_graph(12, labels="zipf", seed=9)
+    cyc = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)]
+    tl, te = [0, 1, 2, 0, 0, 5, 0, 0], cyc + [(2, 5), (5, 6), (3, 7)]
+    runs = []
+    for par in (False, True):
+        oracle.set_parallel(par)
+        try:
+            runs.append(pipeline.run(g.row_ptr, g.col, g.labels, tl, te, max_embeddings=1 << 10))
+        finally:
+            oracle.set_parallel(False)
+    a, b = runs
+    assert not a.count_valid            # the existence passes ran
+    np.testing.assert_array_equal(a.omega, b.omega)
+    np.testing.assert_array_equal(a.A, b.A)
+    np.testing.assert_array_equal(a.omega_pre_final, b.omega_pre_final)
+    assert a.phase_rounds == b.phase_rounds and a.lcc_scanned == b.lcc_scanned
+    assert a.tokens == b.tokens
+    # (entries scanned by the edge pass are not compared: an entry another
+    # thread has already marked is skipped, so that metric depends on timing)

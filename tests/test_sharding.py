@@ -71,7 +71,7 @@ def _worker(rank, world, port, out):
 
 def test_reduce_step_two_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
     costs = [5, 1, 9, 3, 3, 7, 2, 8, 6, 4]

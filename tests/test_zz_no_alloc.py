@@ -67,3 +67,22 @@ def test_noalloc_rejects_graphs_beyond_its_scratch():
     with pytest.raises(ccpm.CcpmError) as ei:
         ccpm.lcc_fixpoint_noalloc(0, rp, col[:0], lab, TL, TE, om, eb)
     assert ei.value.code == ccpm.CCPM_EINVAL and "too large" in str(ei.value)
+
+
+def test_noalloc_rejects_offsets_that_disagree_with_m_dir():
+    # row_ptr[n] larger than the column count the caller states: rejected
+    # before any kernel runs (the scratch is sized from m_dir)
+    import torch
+    from paper_1912_08453_gb300 import ccpm
+    dev = torch.device("cuda:0")
+    g = wl.rmat_graph(10, seed=3)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col[:-64].copy()).to(dev)
+    lab = torch.from_numpy(g.labels).to(dev)
+    om = torch.zeros(g.n, dtype=torch.int32, device=dev)
+    eb = torch.zeros((g.m_dir + 31) // 32, dtype=torch.int32, device=dev)
+    before = torch.cuda.current_device()
+    with pytest.raises(ccpm.CcpmError) as ei:
+        ccpm.lcc_fixpoint_noalloc(0, rp, col, lab, TL, TE, om, eb)
+    assert ei.value.code == ccpm.CCPM_EINVAL and "row_ptr" in str(ei.value)
+    assert torch.cuda.current_device() == before
