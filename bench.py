@@ -56,6 +56,7 @@ METRIC = "template time-to-solution (ms) & edges scanned/s, batched+learned vs p
 C4_BASE = ([20, 30, 40, 20, 50, 60, 30], [(0, 1), (1, 2), (2, 3), (3, 0), (2, 4), (3, 4), (4, 5), (5, 6)])
 C3_TEMPLATE = ([20, 30, 40, 20, 30, 50, 60, 40],
                [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (4, 5), (5, 6), (6, 7), (2, 7)])
+C3_FREQUENT = ([0, 1, 2, 0, 1, 3, 4, 2], C3_TEMPLATE[1])
 TREE6 = ([11, 3, 6, 8, 7, 9], [(0, 1), (1, 2), (1, 3), (3, 4), (4, 5)])
 C4TRI6 = ([5, 12, 11, 11, 5, 7], [(0, 1), (1, 2), (2, 3), (3, 0), (2, 4), (3, 4), (4, 5)])
 
@@ -65,7 +66,12 @@ WORKLOADS = {
            "base": C4_BASE, "batch": 64, "batch_seed": 5},
     # C3: one 8-vertex template with repeated labels and a 5-cycle (TDS) at scale 25
     "c3": {"name": "c3-rmat25-zipf", "scale": 25, "labels": "zipf", "gen": "philox",
-           "templates": {"c3_5cycle8": C3_TEMPLATE}},
+           "templates": {"c3_5cycle8": C3_TEMPLATE},
+           # the LCC phase of the same template shape over the most frequent
+           # labels: about half the vertices start active, so omega (134 MB)
+           # is gathered from everywhere (its full pipeline is out of reach:
+           # the final step over >10^12 matches)
+           "lcc_templates": {"c3_5cycle8_frequent": C3_FREQUENT}},
     # C2: scale 22, degree labels, an LCC-only tree and a 4-cycle + triangle template
     "c2": {"name": "c2-rmat22-degree", "scale": 22, "labels": "degree", "gen": "philox",
            "templates": {"tree6": TREE6, "c4tri6": C4TRI6}},
@@ -392,6 +398,27 @@ def single_template_line(args, cfg, ctx, stream, local, reps=2):
             t.close()
     out["lcc_roofline"] = lcc_roofline(every, cfg["name"])
     out["lcc_first_round"] = lcc_first_round(every)
+    # LCC phase alone (options.lcc_only) of the templates kept for it
+    lcc_counts = []
+    with torch.cuda.stream(stream):
+        for name, (tl, te) in cfg.get("lcc_templates", {}).items():
+            t = ccpm.Template(ctx, tl, te)
+            only = ccpm.options(lcc_only=1)
+            r = ccpm.prune(ctx, graph, t, only)
+            cs = []
+            for _ in range(max(reps, 2)):
+                r, dt = timed(stream, lambda: ccpm.prune(ctx, graph, t, only, result=r))
+                cs.append(r.counts())
+            lcc_counts += cs
+            c = cs[-1]
+            out["templates"][name + "_lcc_phase"] = {
+                "lcc_ms": dt, "rounds": r.phase_rounds(), "active_v_fixpoint": c["active_v"],
+                "lcc_first_round": lcc_first_round([c]), "lcc_roofline": lcc_roofline([c], cfg["name"])}
+            r.close()
+            t.close()
+    if lcc_counts:
+        out["lcc_phase_roofline"] = lcc_roofline(lcc_counts, cfg["name"])
+        out["lcc_phase_first_round"] = lcc_first_round(lcc_counts)
     graph.close()
     del g
     torch.cuda.empty_cache()
@@ -506,6 +533,11 @@ def run_c4(args, cfg):
     roof_lcc = lcc_roofline(counts_plain, cfg["name"])
     roof_search = search_roofline(counts_plain, cfg["name"])
     dominant = roof_search if roof_search["device_ms"] > roof_lcc["device_ms"] else roof_lcc
+    workers = ccpm.batch_tuning(graph)
+    n_graph, m_graph = int(graph.n), int(graph.m)
+    for r in res_all + res_batch + res_bfix + res_plearn:
+        if r is not None:
+            r.close()
 
     graph.close()
     del g
@@ -527,7 +559,7 @@ def run_c4(args, cfg):
             "config": {"workload": cfg["name"],
                        "graph": f"R-MAT scale {cfg['scale']}, edge factor 16, (.57,.19,.19,.05), "
                                 "Zipf(1.2) labels over 64, Philox-generated on the device",
-                       "n": int(graph.n), "m_dir": int(graph.m), "templates": len(hs_all),
+                       "n": n_graph, "m_dir": m_graph, "templates": len(hs_all),
                        "templates_rank0": len(hs), "template_sizes": sorted({t.n0 for t in tmpls_all}),
                        "base_template": {"labels": cfg["base"][0], "edges": cfg["base"][1]},
                        "count_cap": args.count_cap,
@@ -543,7 +575,7 @@ def run_c4(args, cfg):
                                ("ms_lcc", "ms_nlcc", "ms_final", "ms_final_count", "ms_final_vertex",
                                 "ms_final_edge")},
             "counts_valid": int(sum(c["count_valid"] for c in counts_plain)),
-            "workers": int(ccpm.lib.ccpm_graph_batch_workers(graph.h)) if graph.h else None,
+            "autotune": workers,
             "training_records": len(recs), "training_s": train_s, "graph_gen_s": gen_s,
             "search_entries_per_s": search_entries / (total_ms / 1e3) if total_ms > 0 else 0.0,
             "roofline": dominant, "rooflines": [roof_lcc, roof_search],

@@ -112,7 +112,13 @@ typedef struct {
                                    /* untried candidates to other warps: 0 = the   */
                                    /* library default (2048), -1 = never; results  */
                                    /* are the same for every value                 */
-    int      reserved[4];
+    int      lcc_only;             /* 1: stop at the first LCC fixpoint (no non-   */
+                                   /* local constraint, no final search); the     */
+                                   /* result holds that fixpoint                   */
+    int      short_rows;           /* rows up to this many entries are walked 32   */
+                                   /* rows per warp as one stream; longer ones a   */
+                                   /* warp per row: 0 = library default (64)      */
+    int      reserved[2];
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 
@@ -237,17 +243,26 @@ int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
  * workload of Section 6.7: many variants of one query).  Each template's
  * results are exactly those ccpm_prune gives for it.  The templates run
  * concurrently on worker streams of this context, each with its own scratch,
- * so that small phases of different templates overlap on the GPU; the number
- * of workers comes from options.batch_workers or, when 0, from an autotuner
- * that times candidate worker counts on the first call for this graph and
- * keeps the fastest.  outs[i] follows the same create-or-reuse rule as
- * ccpm_prune.  Returns CCPM_OK, CCPM_EBUDGET if any template hit a budget
+ * so that small phases of different templates overlap on the GPU.  With
+ * options.batch_workers = 0 the settings come from an autotuner: on the first
+ * call for this graph it prunes one slice of the batch (its first 8
+ * templates) once per candidate setting and keeps the fastest, choosing in
+ * turn the worker count (4, 8, 16), options.search_split (2048, 512, 8192),
+ * options.short_rows (64, 32, 256) and options.hub_degree (1024, 4096); the
+ * choice is kept on the graph and applies to options left at 0.  Every
+ * setting gives the same results.  outs[i] follows the same create-or-reuse
+ * rule as ccpm_prune.  Returns CCPM_OK, CCPM_EBUDGET if any template hit a budget
  * (see each result's counts), or the first error. */
 int  ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *tmpls,
                       const ccpm_options *opt, ccpm_result_t *outs);
 /* The worker count the autotuner chose for batches over g (0 before the first
  * autotuned ccpm_prune_batch call, or with NULL). */
 int  ccpm_graph_batch_workers(ccpm_graph_t g);
+/* All the autotuner's choices for g (zeros before the first autotuned batch;
+ * 0 for search_split, short_rows or hub_degree = the library default) and
+ * the chosen setting's wall time on the tuning slice in milliseconds. */
+int  ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *search_split, int *short_rows, int *hub_degree,
+                             double *slice_ms);
 
 /* ----------------------------------------------------------------- result */
 

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
                 ("compact", ctypes.c_int), ("search_split", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4),
+                ("lcc_only", ctypes.c_int), ("short_rows", ctypes.c_int), ("reserved", ctypes.c_int * 2),
                 ("mlp", ctypes.c_void_p)]
 
 
@@ -128,6 +128,7 @@ def _load():
         "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
         "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
         "ccpm_graph_batch_workers": ([vp], i32),
+        "ccpm_graph_batch_tuning": ([vp, P(i32), P(i32), P(i32), P(i32), P(ctypes.c_double)], i32),
         "ccpm_result_matches": ([vp, vp, vp, P(Options), vp, ctypes.c_uint64, vp, vp, i32,
                                  P(ctypes.c_uint64)], i32),
         "ccpm_explore": ([vp, vp, vp, i32, P(Options), P(ExploreVariant), i32, P(i32), P(i32),
@@ -155,7 +156,8 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_result_edge_bitmap_device", "ccpm_result_destroy", "ccpm_lcc_fixpoint_noalloc",
             "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
             "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train",
-            "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers", "ccpm_result_matches", "ccpm_explore"]
+            "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers", "ccpm_result_matches", "ccpm_explore",
+            "ccpm_graph_batch_tuning"]
 
 
 def _ptr(a):
@@ -235,6 +237,15 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def batch_tuning(graph) -> dict:
+    """The batch autotuner's choices for `graph` (ccpm_graph_batch_tuning)."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    ms = ctypes.c_double(0.0)
+    lib.ccpm_graph_batch_tuning(graph.h, *[ctypes.byref(x) for x in v], ctypes.byref(ms))
+    return {"workers": v[0].value, "search_split": v[1].value, "short_rows": v[2].value,
+            "hub_degree": v[3].value, "slice_ms": ms.value}
 
 
 class Template:

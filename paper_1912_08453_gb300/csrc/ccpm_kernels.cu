@@ -183,7 +183,7 @@ struct LabelMask { uint32_t m[256]; };
 __global__ void __launch_bounds__(256)
 k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ lab, LabelMask lm,
        const uint32_t *__restrict__ om_in, uint32_t *om0, uint32_t *om1, int32_t *small_out, int32_t *med_out,
-       ChunkItem *chunk_out, HubAcc *acc, RoundStats *st, int hub_deg) {
+       ChunkItem *chunk_out, HubAcc *acc, RoundStats *st, int hub_deg, int short_max) {
     __shared__ uint32_t slm[256];
     __shared__ int32_t sbuf[2][8][32];
     __shared__ int scnt[2][8];
@@ -208,7 +208,7 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
         // buckets: short rows (4 lanes each), medium rows (a warp each), long
         // rows (split into pieces of hub_deg entries); every active vertex is
         // in exactly one of them
-        const int64_t small_max = hub_deg < kSmallDeg ? hub_deg : kSmallDeg;
+        const int64_t small_max = hub_deg < short_max ? hub_deg : short_max;
         bs.push(w && deg <= small_max, (int32_t)v);
         bm.push(w && deg > small_max && deg <= hub_deg, (int32_t)v);
         if (w && deg > hub_deg) {
@@ -2030,7 +2030,9 @@ struct ccpm_graph {
     int32_t *lcol = nullptr;      // rows grouped by neighbour label (built on first search)
     uint8_t *nlab = nullptr;
     std::mutex lrow_mu;           // concurrent batch workers build the grouped rows once
-    int tuned_workers = 0;        // batch worker count chosen by the autotuner
+    int tuned_workers = 0;        // batch settings chosen by the autotuner (0: not tuned yet)
+    int tuned_split = 0, tuned_short = 0, tuned_hub = 0;
+    double tuned_ms = 0.0;        // the chosen setting's time on the tuning slice
     std::atomic<int> prunes{0};   // prunes started on this graph
     std::atomic<bool> lrows_ready{false};   // lcol/nlab built (read without the lock)
 };
@@ -2334,6 +2336,7 @@ struct Pipeline {
     double ms_search_kernel = 0.0;
     int64_t search_launches = 0, nlcc_entries = 0, item_passes = 0;
     int maxc = 0;
+    int short_max = kSmallDeg;      // rows up to this length take the flat short-row path
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
     const int32_t *lcol = nullptr;
@@ -2500,7 +2503,7 @@ struct Pipeline {
         launches++;
         k_init<<<grid_for(ctx, g->n, 256, 8), 256, 0, ctx->stream>>>(g->n, rp, g->lab, all, w.om[cur], w.om[cur],
                                                                      w.om[cur ^ 1], w.small[li], w.med[li],
-                                                                     w.chunk[li], w.acc, w.st, w.hub_deg);
+                                                                     w.chunk[li], w.acc, w.st, w.hub_deg, short_max);
         CU(ctx, cudaGetLastError());
         if (!sync) return CCPM_OK;
         int rc = read_stats();
@@ -2889,6 +2892,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.lrp = g->rp;
     P.lcol = g->col;
     P.lbits = w.ebits;
+    P.short_max = opt.short_rows > 0 ? std::min(opt.short_rows, kMaxHubDeg) : kSmallDeg;
     g->prunes++;
     P.compact_mode = opt.compact;
     cudaStream_t s = ctx->stream;
@@ -2941,7 +2945,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         P.launches++;
         k_init<<<grid, 256, 0, s>>>(g->n, g->rp, g->lab, lm, resume ? r->om : nullptr, w.om[0], w.om[1],
                                     w.small[0], w.med[0],
-                                    w.chunk[0], w.acc, w.st, hub_deg);
+                                    w.chunk[0], w.acc, w.st, hub_deg, P.short_max);
         CUF(cudaGetLastError());
     }
     if (resume) {
@@ -2961,7 +2965,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         return fail(set_err(ctx, CCPM_EOVERFLOW, "hub bookkeeping overflow"));
 
     // ---- LCC to fixpoint (Alg. 4)
-    P.searches_ahead = (int)t.order.size();
+    P.searches_ahead = opt.lcc_only ? 0 : (int)t.order.size();
     int64_t rounds = 0;
     RCF(P.lcc(&rounds));
     r->phase_rounds.push_back((int32_t)rounds);
@@ -2973,6 +2977,10 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     bool over = false;
     int nl_run = 0;
     std::vector<int> remaining = t.order;
+    if (opt.lcc_only) {
+        remaining.clear();
+        opt.run_final = 0;
+    }
     const int n_constraints = (int)remaining.size();
     const bool learned = opt.order_mode == CCPM_ORDER_LEARNED && opt.mlp;
     if (opt.order_mode == CCPM_ORDER_LEARNED && !opt.mlp)
@@ -3480,29 +3488,66 @@ int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *t
     int rc = ensure_label_rows(ctx, g);
     if (rc) return rc;
     int budget_hit = 0;
-    int start = 0;
-    int W = opt.batch_workers > 0 ? opt.batch_workers : g->tuned_workers;
-    if (W <= 0) {
-        // autotune: time candidate worker counts on successive slices of this
-        // batch (every slice's results are final) and keep the fastest per
-        // template; the choice is cached on the graph
-        const int cand[] = {4, 8, 16};
-        const int slice = std::max(1, std::min(T / 4, 8));
-        double best = 1e300;
+    const bool tune = opt.batch_workers <= 0 && g->tuned_workers <= 0;
+    if (tune) {
+        // autotune on one slice of this batch, the same templates for every
+        // candidate (results are the same whatever the setting, so the slice's
+        // results are simply made again): first the worker count, then the
+        // windows a search scans before it hands work on, then the row length
+        // of the flat short-row path, then the piece length of long rows.  The
+        // choice is kept on the graph.
+        const int slice = std::max(1, std::min(T, 8));
+        ccpm_options cand = opt;
+        cand.search_split = 0;
+        cand.short_rows = 0;
+        cand.hub_degree = 0;
         int best_w = 8;
-        for (int c = 0; c < 3 && start + slice <= T; c++) {
+        double best = 1e300;
+        auto time_slice = [&](const ccpm_options &o, int W, double &ms) -> int {
             auto t0 = std::chrono::steady_clock::now();
-            rc = run_batch(ctx, g, start, start + slice, tmpls, &opt, outs, cand[c], &budget_hit);
-            if (rc) return rc;
-            double per = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / slice;
-            if (per < best) { best = per; best_w = cand[c]; }
-            start += slice;
+            int rc2 = run_batch(ctx, g, 0, slice, tmpls, &o, outs, std::min(W, slice), &budget_hit);
+            ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            return rc2;
+        };
+        double ms = 0;
+        int rc;
+        for (int Wc : {4, 8, 16}) {
+            if ((rc = time_slice(cand, Wc, ms))) return rc;
+            if (ms < best) { best = ms; best_w = Wc; }
+        }
+        for (int sp : {512, 8192}) {
+            ccpm_options o = cand;
+            o.search_split = sp;
+            if ((rc = time_slice(o, best_w, ms))) return rc;
+            if (ms < best) { best = ms; cand.search_split = sp; }
+        }
+        for (int sr : {32, 256}) {
+            ccpm_options o = cand;
+            o.short_rows = sr;
+            if ((rc = time_slice(o, best_w, ms))) return rc;
+            if (ms < best) { best = ms; cand.short_rows = sr; }
+        }
+        for (int hd : {4096}) {
+            ccpm_options o = cand;
+            o.hub_degree = hd;
+            if ((rc = time_slice(o, best_w, ms))) return rc;
+            if (ms < best) { best = ms; cand.hub_degree = hd; }
         }
         g->tuned_workers = best_w;
-        W = best_w;
+        g->tuned_split = cand.search_split;
+        g->tuned_short = cand.short_rows;
+        g->tuned_hub = cand.hub_degree;
+        g->tuned_ms = best;
     }
-    if (start < T) {
-        rc = run_batch(ctx, g, start, T, tmpls, &opt, outs, std::min(W, T - start), &budget_hit);
+    int W = opt.batch_workers > 0 ? opt.batch_workers : g->tuned_workers;
+    if (opt.batch_workers <= 0) {
+        // the tuned settings apply where the caller left the library default
+        if (opt.search_split == 0) opt.search_split = g->tuned_split;
+        if (opt.short_rows == 0) opt.short_rows = g->tuned_short;
+        if (opt.hub_degree == 0) opt.hub_degree = g->tuned_hub;
+    }
+    if (T > 0) {
+        int rc = run_batch(ctx, g, 0, T, tmpls, &opt, outs, std::min(W, T), &budget_hit);
         if (rc) return rc;
     }
     if (budget_hit) return set_err(ctx, CCPM_EBUDGET, "a search budget was exceeded in the batch");
@@ -3864,6 +3909,17 @@ const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r) { return r ? r->
 
 int ccpm_graph_batch_workers(ccpm_graph_t g) { return g ? g->tuned_workers : 0; }
 
+int ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *search_split, int *short_rows, int *hub_degree,
+                            double *slice_ms) {
+    if (!g) return CCPM_EINVAL;
+    if (workers) *workers = g->tuned_workers;
+    if (search_split) *search_split = g->tuned_split;
+    if (short_rows) *short_rows = g->tuned_short;
+    if (hub_degree) *hub_degree = g->tuned_hub;
+    if (slice_ms) *slice_ms = g->tuned_ms;
+    return CCPM_OK;
+}
+
 void ccpm_result_destroy(ccpm_result_t r) {
     if (!r) return;
     cudaSetDevice(r->g->ctx->device);
@@ -4166,7 +4222,7 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         if (m_dir & 31) k_set_word<<<1, 1, 0, s>>>(ebits + words - 1, (1u << (uint32_t)(m_dir & 31)) - 1u);
     }
     k_init<<<grid(n, 256), 256, 0, s>>>(n, row_ptr, labels, lm, nullptr, om[0], om[1], small[0], med[0], chunk[0], acc,
-                                        st, hub);
+                                        st, hub, kSmallDeg);
     NA_CU(cudaGetLastError());
     NA_CU(read_stats());
     if (hs.n_hub_slots > (unsigned)L.acc_cap || (int64_t)hs.n_chunk > L.chunk_cap)

@@ -207,6 +207,12 @@ def test_batch_equals_one_at_a_time(ctx):
     hs = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls]
     for workers in (0, 3):
         res = ccpm.prune_batch(ctx, graph, hs, ccpm.options(batch_workers=workers))
+        if workers == 0:
+            # the autotuner chose and recorded every setting it tunes
+            tune = ccpm.batch_tuning(graph)
+            assert tune["workers"] in (4, 8, 16) and tune["search_split"] in (0, 512, 8192)
+            assert tune["short_rows"] in (0, 32, 256) and tune["hub_degree"] in (0, 4096)
+            assert tune["slice_ms"] > 0
         for t, h, r in zip(tmpls, hs, res):
             one = ccpm.prune(ctx, graph, h)
             np.testing.assert_array_equal(r.omega(), one.omega())
