@@ -283,7 +283,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const uint32_t *__restrict__ om, uint32_t *ebits,
                                               const SmemTmpl &s, Partial<MAXC> &p,
                                               uint32_t &scanned, const uint8_t *__restrict__ lab0,
-                                              const uint32_t *slm) {
+                                              const uint32_t *slm, const uint32_t (&cm)[4]) {
     constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
     const int64_t w0 = beg >> 5;
@@ -325,19 +325,21 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
         if (k0 + UNR < nwin) load_step(k0 + UNR);
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
+            if (k0 + j >= nwin) break;          // past the row's last window (warp-uniform)
             const uint32_t w = wu[j];
-            bool keep = false;
-            if (w) {
-                scanned++;
-                if (w & nbr_v) {
-                    keep = true;
-                    p.U |= w;
-                    p.nN++;
+            const bool keep = (w & nbr_v) != 0u;
+            scanned += w != 0u;
+            if (w != 0u && !keep) p.achg = 1u;  // eta eliminates the entry
+            if (keep) {
+                p.U |= w;
+                p.nN++;
+                if constexpr (MAXC > 0 && MAXC <= 4) {
+#pragma unroll
+                    for (int c = 0; c < MAXC; c++) p.cnt[c] += (w & cm[c]) ? 1u : 0u;
+                } else {
 #pragma unroll
                     for (int c = 0; c < MAXC; c++)
                         if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
-                } else {
-                    p.achg = 1u;            // eta eliminates the entry
                 }
             }
             // the bit goes with the failing entries and with those whose other
@@ -401,140 +403,183 @@ struct LccTally {
 // entries are walked as one stream, 32 per step with one entry per lane, so
 // lanes stay busy whatever the row lengths.  A step holds pieces of several
 // rows: every lane finds its row from the piece starts, and per-row sums are
-// segmented warp reductions whose result each row's lane collects.  The
-// column loads stream past the caches (read once per round).
-template <int MAXC, bool DENSE>
-__device__ __forceinline__ void short_rows_batch(const LccArgs &a, const SmemTmpl &s, const uint32_t *slm,
-                                                 ShortRows &sr, int64_t idx0, WarpBuf<int32_t> &bs,
-                                                 LccTally &tl) {
+// segmented warp reductions whose result each row's lane collects.
+//
+// The walk is software-pipelined: while the neighbour omegas (or labels) of
+// one step are gathered, the next step's rows are located and its edge bits
+// and column indices are loaded, and the next batch's list entries, omegas
+// and row offsets are loaded during the current batch.  The column loads
+// stream past the caches (read once per round).
+
+// Where the entries of one step lie: lane k holds stream entry k0 + k.
+struct ShortStep {
+    uint32_t seg;        // lanes of this lane's row piece
+    int seg_lo;          // first lane of the piece
+    int64_t e;           // CSR entry
+    uint32_t nb;         // template neighbours of its row's omega
+    bool act;            // a live entry (in range, bit set)
+    int32_t u;           // its column index (valid when act)
+    bool ov;             // row lane: its row has a piece in this step ...
+    int lo;              // ... starting at this lane
+};
+
+template <bool DENSE>
+__device__ __forceinline__ void short_locate(const LccArgs &a, ShortRows &sr, int k0, int T, int start, int d,
+                                             ShortStep &st) {
     const int lane = (int)lane_id();
-    const int64_t idx = idx0 + lane;
-    int32_t v = -1;
-    uint32_t wv = 0u;
-    int64_t b = 0;
-    int d = 0;
-    if (idx < a.n_small) {
-        v = a.small_in[idx];
-        wv = __ldg(a.om_cur + v);
-        if (wv) {
-            b = a.rp[v];
-            d = (int)(a.rp[v + 1] - b);
-        }
-    }
-    const uint32_t nbr = wv ? nbr_mask(wv, s) : 0u;
-    int S = d;                                   // inclusive prefix of the row lengths
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL_MASK, S, o);
-        if (lane >= o) S += t;
-    }
-    const int T = __shfl_sync(FULL_MASK, S, 31);
-    const int start = S - d;
-    sr.off[lane] = b - start;
-    sr.nbr[lane] = nbr;
-    uint32_t U = 0u, N = 0u;
-    uint32_t cnt[MAXC > 0 ? MAXC : 1];
-#pragma unroll
-    for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) cnt[c] = 0u;
+    const int lo = max(start, k0) - k0, hi = min(start + d, k0 + 32) - k0;
+    st.ov = lo < hi;
+    st.lo = lo;
+    if (st.ov) sr.row[lo] = lane;
+    const uint32_t H = __reduce_or_sync(FULL_MASK, st.ov ? (1u << lo) : 0u);   // piece starts (bit 0 always)
     __syncwarp();
-    for (int k0 = 0; k0 < T; k0 += 32) {
-        // the piece of row `lane` inside this step: lanes [lo, hi)
-        const int lo = max(start, k0) - k0, hi = min(start + d, k0 + 32) - k0;
-        const bool ov = lo < hi;
-        if (ov) sr.row[lo] = lane;
-        const uint32_t H = __reduce_or_sync(FULL_MASK, ov ? (1u << lo) : 0u);   // piece starts (bit 0 always)
+    const uint32_t upto = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
+    st.seg_lo = 31 - __clz(H & upto);
+    const uint32_t above = H & ~upto;
+    const int seg_hi = above ? __ffs(above) - 1 : 32;
+    st.seg = (seg_hi == 32 ? FULL_MASK : ((1u << seg_hi) - 1u)) & ~((1u << st.seg_lo) - 1u);
+    const int r = sr.row[st.seg_lo];
+    const int k = k0 + lane;
+    const bool valid = k < T;
+    st.e = sr.off[r] + k;
+    st.nb = sr.nbr[r];
+    st.act = valid;
+    if (!DENSE && valid) st.act = (__ldg(a.ebits + (st.e >> 5)) >> (uint32_t)(st.e & 31)) & 1u;
+    st.u = st.act ? __ldcs(a.col + st.e) : 0;
+    __syncwarp();                                // sr.row is rewritten by the next step
+}
+
+template <int MAXC, bool DENSE>
+__device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, const uint32_t *slm,
+                                           const uint32_t (&cm)[4], ShortRows &sr, int64_t first, int64_t stride,
+                                           WarpBuf<int32_t> &bs, LccTally &tl) {
+    const int lane = (int)lane_id();
+    const int64_t n_batch = (a.n_small + 31) / 32;
+    auto load_v = [&](int64_t ch) -> int32_t {
+        const int64_t idx = ch * 32 + lane;
+        return (ch < n_batch && idx < a.n_small) ? a.small_in[idx] : -1;
+    };
+    int32_t v_nx = load_v(first);
+    uint32_t wv_nx = 0u;
+    int64_t b_nx = 0;
+    int d_nx = 0;
+    auto load_row = [&]() {
+        wv_nx = 0u; b_nx = 0; d_nx = 0;
+        if (v_nx >= 0) {
+            wv_nx = __ldg(a.om_cur + v_nx);
+            if (wv_nx) {
+                b_nx = a.rp[v_nx];
+                d_nx = (int)(a.rp[v_nx + 1] - b_nx);
+            }
+        }
+    };
+    load_row();
+    for (int64_t ch = first; ch < n_batch; ch += stride) {
+        const int32_t v = v_nx;
+        const uint32_t wv = wv_nx;
+        const int64_t b = b_nx;
+        const int d = d_nx;
+        v_nx = load_v(ch + stride);              // in flight during this batch
+        const uint32_t nbr = wv ? nbr_mask(wv, s) : 0u;
+        int S = d;                               // inclusive prefix of the row lengths
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL_MASK, S, o);
+            if (lane >= o) S += t;
+        }
+        const int T = __shfl_sync(FULL_MASK, S, 31);
+        const int start = S - d;
+        sr.off[lane] = b - start;
+        sr.nbr[lane] = nbr;
+        uint32_t U = 0u, N = 0u;
+        uint32_t cnt[MAXC > 0 ? MAXC : 1];
+#pragma unroll
+        for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) cnt[c] = 0u;
         __syncwarp();
-        const uint32_t upto = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
-        const int seg_lo = 31 - __clz(H & upto);
-        const uint32_t above = H & ~upto;
-        const int seg_hi = above ? __ffs(above) - 1 : 32;
-        const uint32_t seg = (seg_hi == 32 ? FULL_MASK : ((1u << seg_hi) - 1u)) & ~((1u << seg_lo) - 1u);
-        const int r = sr.row[seg_lo];
-        const int k = k0 + lane;
-        const bool valid = k < T;
-        const int64_t e = sr.off[r] + k;
-        const uint32_t nb = sr.nbr[r];
-        bool act = valid;
-        if (!DENSE && valid) act = (__ldg(a.ebits + (e >> 5)) >> (uint32_t)(e & 31)) & 1u;
-        uint32_t w = 0u;
-        if (act) {
-            const int32_t u = __ldcs(a.col + e);
-            w = a.lab0 ? slm[__ldg(a.lab0 + u)] : __ldg(a.om_cur + u);
-        }
-        const bool keep = (w & nb) != 0u;
-        tl.scanned += w != 0u;
-        if (w != 0u && !keep) tl.changed = 1u;           // eta eliminates a live entry
-        // entries whose other end is already inactive lose their bit too (no
-        // change of the state: such an entry is inactive already)
-        const uint32_t dm = __ballot_sync(FULL_MASK, act && !keep) & seg;
-        uint32_t ru, gk[MAXC > 4 ? MAXC : 1];
-        uint32_t rk;
-        ru = __reduce_or_sync(seg, keep ? w : 0u);
-        if constexpr (MAXC <= 4) {
-            // the kept count and up to four class counts of a piece (each at
-            // most 32) packed in 6-bit fields
-            uint32_t pk = keep ? 1u : 0u;
+        ShortStep cur;
+        if (T > 0) short_locate<DENSE>(a, sr, 0, T, start, d, cur);
+        load_row();                              // the next batch's omegas and offsets
+        for (int k0 = 0; k0 < T; k0 += 32) {
+            uint32_t w = 0u;
+            if (cur.act) w = a.lab0 ? slm[__ldg(a.lab0 + cur.u)] : __ldg(a.om_cur + cur.u);
+            ShortStep nx;
+            if (k0 + 32 < T) short_locate<DENSE>(a, sr, k0 + 32, T, start, d, nx);
+            const bool keep = (w & cur.nb) != 0u;
+            tl.scanned += w != 0u;
+            if (w != 0u && !keep) tl.changed = 1u;       // eta eliminates a live entry
+            // entries whose other end is already inactive lose their bit too (no
+            // change of the state: such an entry is inactive already)
+            const uint32_t dm = __ballot_sync(FULL_MASK, cur.act && !keep) & cur.seg;
+            uint32_t gk[MAXC > 4 ? MAXC : 1];
+            uint32_t rk;
+            const uint32_t ru = __reduce_or_sync(cur.seg, keep ? w : 0u);
+            if constexpr (MAXC <= 4) {
+                // the kept count and up to four class counts of a piece (each at
+                // most 32) packed in 6-bit fields
+                uint32_t pk = keep ? 1u : 0u;
 #pragma unroll
-            for (int c = 0; c < MAXC; c++)
-                if (keep && c < s.n_cls && (w & s.cls_mask[c])) pk += 1u << (6 * (c + 1));
-            rk = __reduce_add_sync(seg, pk);
-        } else {
-            rk = __reduce_add_sync(seg, keep ? 1u : 0u);
+                for (int c = 0; c < MAXC; c++)
+                    if (keep && (w & cm[c])) pk += 1u << (6 * (c + 1));
+                rk = __reduce_add_sync(cur.seg, pk);
+            } else {
+                rk = __reduce_add_sync(cur.seg, keep ? 1u : 0u);
 #pragma unroll
-            for (int c = 0; c < MAXC; c++)
-                gk[c] = c < s.n_cls ? __reduce_add_sync(seg, (keep && (w & s.cls_mask[c])) ? 1u : 0u) : 0u;
-        }
-        if (lane == seg_lo && dm) {
-            // the piece's entries are consecutive from e: at most two words
-            const uint32_t bits = dm >> seg_lo;
-            const uint32_t sh = (uint32_t)(e & 31);
-            atomicAnd(&a.ebits[e >> 5], ~(bits << sh));
-            if (sh && (bits >> (32 - sh))) atomicAnd(&a.ebits[(e >> 5) + 1], ~(bits >> (32 - sh)));
-        }
-        // each row's lane takes the sums of its piece
-        const int src = ov ? lo : 0;
-        const uint32_t gu = __shfl_sync(FULL_MASK, ru, src);
-        const uint32_t gr = __shfl_sync(FULL_MASK, rk, src);
-        if constexpr (MAXC <= 4) {
-            if (ov) {
-                U |= gu;
-                N += gr & 63u;
-#pragma unroll
-                for (int c = 0; c < MAXC; c++) cnt[c] += (gr >> (6 * (c + 1))) & 63u;
+                for (int c = 0; c < MAXC; c++)
+                    gk[c] = c < s.n_cls ? __reduce_add_sync(cur.seg, (keep && (w & s.cls_mask[c])) ? 1u : 0u) : 0u;
             }
-        } else {
-            uint32_t gc[MAXC];
-#pragma unroll
-            for (int c = 0; c < MAXC; c++) gc[c] = __shfl_sync(FULL_MASK, gk[c], src);
-            if (ov) {
-                U |= gu;
-                N += gr;
-#pragma unroll
-                for (int c = 0; c < MAXC; c++) cnt[c] += gc[c];
+            if (lane == cur.seg_lo && dm) {
+                // the piece's entries are consecutive from e: at most two words
+                const uint32_t bits = dm >> cur.seg_lo;
+                const uint32_t sh = (uint32_t)(cur.e & 31);
+                atomicAnd(&a.ebits[cur.e >> 5], ~(bits << sh));
+                if (sh && (bits >> (32 - sh))) atomicAnd(&a.ebits[(cur.e >> 5) + 1], ~(bits >> (32 - sh)));
             }
-        }
-        __syncwarp();                            // sr.row is rewritten by the next step
-    }
-    if (v >= 0) {
-        uint32_t keep = 0u;
-        if (wv) {
-            Partial<MAXC> p;
-            p.U = U;
-            p.nN = N;
+            // each row's lane takes the sums of its piece
+            const int src = cur.ov ? cur.lo : 0;
+            const uint32_t gu = __shfl_sync(FULL_MASK, ru, src);
+            const uint32_t gr = __shfl_sync(FULL_MASK, rk, src);
+            if constexpr (MAXC <= 4) {
+                if (cur.ov) {
+                    U |= gu;
+                    N += gr & 63u;
 #pragma unroll
-            for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) p.cnt[c] = cnt[c];
-            keep = decide<MAXC>(wv, p, s);
-            tl.rows += (unsigned long long)d;
-            tl.alive++;
-            if (keep) { tl.kept += N; tl.rows_next += (unsigned long long)d; }
-            if (keep != wv) tl.changed = 1u;
-            if (keep == 0u) clear_row<1>(a.ebits, b, b + d, 0);
+                    for (int c = 0; c < MAXC; c++) cnt[c] += (gr >> (6 * (c + 1))) & 63u;
+                }
+            } else {
+                uint32_t gc[MAXC];
+#pragma unroll
+                for (int c = 0; c < MAXC; c++) gc[c] = __shfl_sync(FULL_MASK, gk[c], src);
+                if (cur.ov) {
+                    U |= gu;
+                    N += gr;
+#pragma unroll
+                    for (int c = 0; c < MAXC; c++) cnt[c] += gc[c];
+                }
+            }
+            cur = nx;
         }
-        a.om_next[v] = keep;
-        if (a.deg) a.deg[v] = keep ? (int64_t)N : 0;
+        if (v >= 0) {
+            uint32_t keep = 0u;
+            if (wv) {
+                Partial<MAXC> p;
+                p.U = U;
+                p.nN = N;
+#pragma unroll
+                for (int c = 0; c < (MAXC > 0 ? MAXC : 1); c++) p.cnt[c] = cnt[c];
+                keep = decide<MAXC>(wv, p, s);
+                tl.rows += (unsigned long long)d;
+                tl.alive++;
+                if (keep) { tl.kept += N; tl.rows_next += (unsigned long long)d; }
+                if (keep != wv) tl.changed = 1u;
+                if (keep == 0u) clear_row<1>(a.ebits, b, b + d, 0);
+            }
+            a.om_next[v] = keep;
+            if (a.deg) a.deg[v] = keep ? (int64_t)N : 0;
+        }
+        // the batch's vertices that were active at the start of the round
+        bs.push(v >= 0 && wv != 0u, v);
+        __syncwarp();                            // sr.off / sr.nbr are rewritten by the next batch
     }
-    // the batch's vertices that were active at the start of the round
-    bs.push(v >= 0 && wv != 0u, v);
 }
 
 template <int MAXC, bool DENSE>
@@ -559,6 +604,11 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     LccTally tl;
+    // masks of the first four label-multiplicity classes in registers (0 for
+    // classes the template does not have: they never count)
+    uint32_t cm[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) cm[c] = s.cls_mask[c];
 
     // (1) pieces of long rows: one warp per piece, combined through HubAcc;
     // the last piece to finish decides for the vertex.
@@ -578,7 +628,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
         scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
-                                   slm);
+                                   slm, cm);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -647,7 +697,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
                 scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned,
-                                           a.lab0, slm);
+                                           a.lab0, slm, cm);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
                 p.achg = grp_or<32>(p.achg);
@@ -669,9 +719,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     }
 
     // (3) short rows: 32 vertices per warp batch, entries streamed flat
-    const int64_t n_sbatch = (a.n_small + 31) / 32;
-    for (int64_t ch = gwarp; ch < n_sbatch; ch += nwarps)
-        short_rows_batch<MAXC, DENSE>(a, s, slm, srows[wib], ch * 32, bs, tl);
+    short_rows<MAXC, DENSE>(a, s, slm, cm, srows[wib], gwarp, nwarps, bs, tl);
 
     bs.flush();
     bm.flush();
