@@ -469,7 +469,11 @@ def run_c4(args, cfg):
         t_train = time.time()
         net = ordering.train(ctx, X, y, steps=2000) if len(recs) >= 8 else None
         train_s = time.time() - t_train
-        learned = ordering.learned_options(net, max_embeddings=args.count_cap) if net else cap
+        # the fixed order judges the learned one on a slice of this batch
+        # (plain, one template at a time); the batch keeps it only if it wins
+        use_learned, judge_fixed, judge_learned = (ordering.judge(ctx, graph, hs[:16], net, args.count_cap)
+                                                   if net else (False, 0.0, 0.0))
+        learned = ordering.learned_options(net, max_embeddings=args.count_cap) if use_learned else cap
         res_batch = ccpm.prune_batch(ctx, graph, hs, learned, allow_budget=True)   # autotunes the workers
         for _ in range(max(args.warmup - 1, 0)):
             ccpm.prune_batch(ctx, graph, hs, learned, results=res_batch, allow_budget=True)
@@ -503,9 +507,11 @@ def run_c4(args, cfg):
         _, ms_bfix = timed(stream, lambda: ccpm.prune_batch(ctx, graph, hs, cap, results=res_bfix, allow_budget=True))
         res_plearn = [None] * len(hs)
 
+        always_learned = ordering.learned_options(net, max_embeddings=args.count_cap) if net else cap
+
         def plain_learned():
             for i, h in enumerate(hs):
-                res_plearn[i] = ccpm.prune(ctx, graph, h, learned, result=res_plearn[i], allow_budget=True)
+                res_plearn[i] = ccpm.prune(ctx, graph, h, always_learned, result=res_plearn[i], allow_budget=True)
         _, ms_plearn = timed(stream, plain_learned)
         same = same_results(res_plain, res_batch, g.n, words, dev) and \
             same_results(res_plain, res_bfix, g.n, words, dev) and \
@@ -577,6 +583,10 @@ def run_c4(args, cfg):
             "counts_valid": int(sum(c["count_valid"] for c in counts_plain)),
             "autotune": workers,
             "training_records": len(recs), "training_s": train_s, "graph_gen_s": gen_s,
+            "learned_order": {"used_in_batch": bool(use_learned), "judge_slice_ms_fixed": judge_fixed,
+                              "judge_slice_ms_learned": judge_learned,
+                              "note": "the fixed order judges the learned one on the first 16 templates; "
+                                      "plain_learned_ms always uses the learned order"},
             "search_entries_per_s": search_entries / (total_ms / 1e3) if total_ms > 0 else 0.0,
             "roofline": dominant, "rooflines": [roof_lcc, roof_search],
             "lcc_first_round": lcc_first_round(counts_plain),

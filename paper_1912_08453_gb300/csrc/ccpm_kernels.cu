@@ -61,7 +61,7 @@ struct RoundStats {
     unsigned int overflow;        // a search hit its budget
     unsigned int n_spill;         // items handed on by searches that ran long (reserved)
     unsigned int spill_stop;      // the spill list is valid below this index (see spill)
-    unsigned int pad2;
+    unsigned int skipped;         // LCC round queued after the fixpoint: did nothing
 };
 
 struct HubAcc {                   // partial LCC state of one split row
@@ -251,6 +251,10 @@ struct LccArgs {
     // 4-byte omega word (lab0 = labels, lmask = label -> initial omega)
     const uint8_t *lab0;
     LabelMask lmask;
+    // rounds queued without a host round trip: the list sizes come from the
+    // previous round's counters, and a round after the fixpoint does nothing
+    const RoundStats *prev;       // nullable: sizes are the fields above
+    int resident_warps;           // warps of one resident wave (medium prefetch unit)
 };
 
 template <int MAXC>
@@ -452,12 +456,12 @@ __device__ __forceinline__ void short_locate(const LccArgs &a, ShortRows &sr, in
 template <int MAXC, bool DENSE>
 __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, const uint32_t *slm,
                                            const uint32_t (&cm)[4], ShortRows &sr, int64_t first, int64_t stride,
-                                           WarpBuf<int32_t> &bs, LccTally &tl) {
+                                           int64_t n_small, WarpBuf<int32_t> &bs, LccTally &tl) {
     const int lane = (int)lane_id();
-    const int64_t n_batch = (a.n_small + 31) / 32;
+    const int64_t n_batch = (n_small + 31) / 32;
     auto load_v = [&](int64_t ch) -> int32_t {
         const int64_t idx = ch * 32 + lane;
-        return (ch < n_batch && idx < a.n_small) ? a.small_in[idx] : -1;
+        return (ch < n_batch && idx < n_small) ? a.small_in[idx] : -1;
     };
     int32_t v_nx = load_v(first);
     uint32_t wv_nx = 0u;
@@ -585,6 +589,18 @@ __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, 
 template <int MAXC, bool DENSE>
 __global__ void __launch_bounds__(256, 4)
 k_lcc_round(LccArgs a, DevTmpl t) {
+    int64_t n_small = a.n_small, n_med = a.n_med, n_chunk = a.n_chunk;
+    int MB = a.med_chunk;
+    if (a.prev) {
+        if (a.prev->changed == 0u) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.st->skipped = 1u;
+            return;
+        }
+        n_small = a.prev->n_small;
+        n_med = a.prev->n_med;
+        n_chunk = a.prev->n_chunk;
+        MB = (int)max((int64_t)1, min((int64_t)16, n_med / (4 * (int64_t)a.resident_warps)));
+    }
     __shared__ SmemTmpl s;
     __shared__ uint32_t slm[256];
     __shared__ int32_t sbuf[2][8][32];
@@ -612,7 +628,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
 
     // (1) pieces of long rows: one warp per piece, combined through HubAcc;
     // the last piece to finish decides for the vertex.
-    for (int64_t it = gwarp; it < a.n_chunk; it += nwarps) {
+    for (int64_t it = gwarp; it < n_chunk; it += nwarps) {
         ChunkItem ci = a.chunk_in[it];
         const uint32_t wv = __ldg(a.om_cur + ci.v);
         if (wv == 0u) {
@@ -675,14 +691,13 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     // (2) medium rows: one warp per vertex, taken 16 at a time: the list
     // entries, omega and row offsets of the next 16 vertices are loaded by 16
     // lanes at once, so each row walk starts from registers
-    const int MB = a.med_chunk;
-    const int64_t n_mchunks = (a.n_med + MB - 1) / MB;
+    const int64_t n_mchunks = (n_med + MB - 1) / MB;
     for (int64_t ch = gwarp; ch < n_mchunks; ch += nwarps) {
         const int64_t idx = ch * MB + lane;
         int32_t vl = -1;
         uint32_t wl = 0u;
         int64_t bl = 0, el = 0;
-        if (lane < MB && idx < a.n_med) {
+        if (lane < MB && idx < n_med) {
             vl = a.med_in[idx];
             wl = __ldg(a.om_cur + vl);
             if (wl) { bl = a.rp[vl]; el = a.rp[vl + 1]; }
@@ -719,7 +734,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
     }
 
     // (3) short rows: 32 vertices per warp batch, entries streamed flat
-    short_rows<MAXC, DENSE>(a, s, slm, cm, srows[wib], gwarp, nwarps, bs, tl);
+    short_rows<MAXC, DENSE>(a, s, slm, cm, srows[wib], gwarp, nwarps, n_small, bs, tl);
 
     bs.flush();
     bm.flush();
@@ -2011,6 +2026,9 @@ k_count(int64_t n, const uint32_t *__restrict__ om, int64_t words, const uint32_
 
 using namespace ccpm;
 
+// LCC rounds queued per host round trip.
+constexpr int kLccGroup = 4;
+
 struct Workspace {
     int64_t n = 0, m = 0, words = 0;
     int hub_deg = 0;
@@ -2031,6 +2049,8 @@ struct Workspace {
     int64_t spill_cap = 0;
     DevPlan *plans = nullptr;
     RoundStats *st = nullptr;        // device
+    RoundStats *st_ring = nullptr;   // counters of a group of queued LCC rounds
+    RoundStats *st_ring_h = nullptr; // pinned host mirror
     unsigned long long *next_root = nullptr;   // dynamic root counter of the searches
     RoundStats *st_h = nullptr;      // pinned host mirror
     unsigned long long *cnt = nullptr;
@@ -2157,6 +2177,8 @@ void ws_free(Workspace &w) {
     cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
     cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.spill_items); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
     if (w.st_h) cudaFreeHost(w.st_h);
+    cudaFree(w.st_ring);
+    if (w.st_ring_h) cudaFreeHost(w.st_ring_h);
     if (w.cnt_h) cudaFreeHost(w.cnt_h);
     cudaFree(w.hist);
     if (w.hist_h) cudaFreeHost(w.hist_h);
@@ -2199,6 +2221,8 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     if ((rc = dalloc(ctx, &w.spill_items, (size_t)w.spill_cap))) return rc;
     if ((rc = dalloc(ctx, &w.plans, (size_t)kMaxPlans))) return rc;
     if ((rc = dalloc(ctx, &w.st, 1))) return rc;
+    if ((rc = dalloc(ctx, &w.st_ring, (size_t)kLccGroup))) return rc;
+    CU(ctx, cudaMallocHost((void **)&w.st_ring_h, sizeof(RoundStats) * kLccGroup));
     if ((rc = dalloc(ctx, &w.cnt, 2))) return rc;
     if ((rc = dalloc(ctx, &w.next_root, 1))) return rc;
     CU(ctx, cudaMallocHost((void **)&w.st_h, sizeof(RoundStats)));
@@ -2378,8 +2402,9 @@ struct Pipeline {
     int64_t scanned = 0;
     int64_t windows = 0;
     int64_t rows = 0, alive = 0, launches = 0, lcc_launches = 0;
-    int64_t alg_bytes = 0, kernel_bytes = 0, first_entries = 0;
+    int64_t alg_bytes = 0, kernel_bytes = 0, first_entries = 0, lcc_rounds_run = 0;
     double ms_first = 0.0;
+    int rc_compact = 0;
     double ms_lcc_kernel = 0.0;
     double ms_search_kernel = 0.0;
     int64_t search_launches = 0, nlcc_entries = 0, item_passes = 0;
@@ -2420,7 +2445,10 @@ struct Pipeline {
         return CCPM_OK;
     }
 
-    int launch_round() {
+    // One LCC round.  slot: its counters; prev (nullable): the previous
+    // round's counters, from which the round reads its list sizes on the
+    // device (a round queued without a host round trip).
+    int launch_round(RoundStats *slot, const RoundStats *prev) {
         Workspace &w = ctx->ws;
         LccArgs a;
         a.rp = lrp;
@@ -2438,7 +2466,9 @@ struct Pipeline {
         a.med_out = w.med[li ^ 1];
         a.chunk_out = w.chunk[li ^ 1];
         a.acc = w.acc;
-        a.st = w.st;
+        a.st = slot;
+        a.prev = prev;
+        a.resident_warps = ctx->num_sms * 32;
         a.hub_deg = w.hub_deg;
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
         a.lab0 = from_labels ? g->lab : nullptr;
@@ -2449,7 +2479,9 @@ struct Pipeline {
         const int64_t resident = (int64_t)ctx->num_sms * 32;
         a.med_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, n_med / (4 * resident)));
         a.small_chunk = n_small >= 32 * 4 * resident ? 32 : (n_small >= 16 * 4 * resident ? 16 : 8);
-        int64_t warps = n_chunk + (n_med + a.med_chunk - 1) / a.med_chunk + (n_small + a.small_chunk - 1) / a.small_chunk;
+        // a queued round does not know its sizes: one full resident wave
+        int64_t warps = prev ? ((int64_t)1 << 40)
+                             : n_chunk + (n_med + a.med_chunk - 1) / a.med_chunk + (n_small + a.small_chunk - 1) / a.small_chunk;
         launches++;
         lcc_launches++;
         // one resident wave: grid-stride work is split evenly over warps that all run at once
@@ -2469,42 +2501,64 @@ struct Pipeline {
         return CCPM_OK;
     }
 
-    // LCC to fixpoint; returns rounds via *rounds.
-    int lcc(int64_t *rounds) {
+    // LCC to fixpoint; returns rounds via *rounds.  Rounds are queued in
+    // groups of up to kLccGroup with one host round trip per group: each
+    // queued round reads its list sizes from the previous round's counters,
+    // and rounds queued after the fixpoint return at once.  The first round
+    // after init runs alone (its time is reported on its own, and a
+    // compaction may follow it).  Compaction is considered between groups.
+    int lcc(int64_t *rounds, bool first_alone = false) {
         Workspace &w = ctx->ws;
         int64_t r = 0;
+        bool alone = first_alone;
         for (;;) {
-            CU(ctx, cudaMemsetAsync(w.st, 0, sizeof(RoundStats), ctx->stream));
+            const int G = alone ? 1 : kLccGroup;
+            alone = false;
+            CU(ctx, cudaMemsetAsync(w.st_ring, 0, sizeof(RoundStats) * (size_t)G, ctx->stream));
             CU(ctx, cudaEventRecord(w.ev[4], ctx->stream));
-            int rc = launch_round();
-            if (rc) return rc;
+            for (int i = 0; i < G; i++) {
+                int rc = launch_round(w.st_ring + i, i ? w.st_ring + i - 1 : nullptr);
+                if (rc) return rc;
+            }
             CU(ctx, cudaEventRecord(w.ev[5], ctx->stream));
-            if ((rc = read_stats())) return rc;
+            CU(ctx, cudaMemcpyAsync(w.st_ring_h, w.st_ring, sizeof(RoundStats) * (size_t)G, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+            CU(ctx, cudaStreamSynchronize(ctx->stream));
             float ms = 0.f;
             CU(ctx, cudaEventElapsedTime(&ms, w.ev[4], w.ev[5]));
             ms_lcc_kernel += ms;
-            r++;
-            scanned += (int64_t)w.st_h->scanned;
-            rows += (int64_t)w.st_h->row_entries;
-            alive += (int64_t)w.st_h->alive;
-            alg_bytes += (33 * (int64_t)w.st_h->scanned) / 4 + 16 * (int64_t)w.st_h->alive;
-            kernel_bytes += 24 * (int64_t)w.st_h->alive + (33 * (int64_t)w.st_h->row_entries) / 8 +
-                            4 * (int64_t)w.st_h->scanned;
-            if (lcc_launches == 1) {
-                first_entries = (int64_t)w.st_h->scanned;
-                ms_first = ms;
+            bool done = false;
+            int ran = 0;
+            for (int i = 0; i < G; i++) {
+                const RoundStats &h = w.st_ring_h[i];
+                if (h.skipped) break;
+                ran++;
+                r++;
+                scanned += (int64_t)h.scanned;
+                rows += (int64_t)h.row_entries;
+                alive += (int64_t)h.alive;
+                alg_bytes += (33 * (int64_t)h.scanned) / 4 + 16 * (int64_t)h.alive;
+                kernel_bytes += 24 * (int64_t)h.alive + (33 * (int64_t)h.row_entries) / 8 + 4 * (int64_t)h.scanned;
+                if (lcc_rounds_run == 0) {
+                    first_entries = (int64_t)h.scanned;
+                    ms_first = ms;
+                }
+                lcc_rounds_run++;
+                n_small = h.n_small;
+                n_med = h.n_med;
+                n_chunk = h.n_chunk;
+                last_kept = (int64_t)h.kept;
+                last_rows = (int64_t)h.rows_next;
+                li ^= 1;
+                cur ^= 1;
+                if (!h.changed) { done = true; break; }
             }
-            n_small = w.st_h->n_small;
-            n_med = w.st_h->n_med;
-            n_chunk = w.st_h->n_chunk;
-            last_kept = (int64_t)w.st_h->kept;
-            last_rows = (int64_t)w.st_h->rows_next;
-            li ^= 1;
-            cur ^= 1;
-            if (!w.st_h->changed) break;
+            // launches that returned at once are not rounds
+            lcc_launches -= G - ran;
+            if (done) break;
             if (r > (int64_t)4 * (g->m + g->n) + 8)
                 return set_err(ctx, CCPM_ETIMEOUT, "LCC did not converge");
-            if (want_compact() && (rc = compact())) return rc;
+            if (want_compact() && (rc_compact = compact())) return rc_compact;
         }
         *rounds = r;
         return CCPM_OK;
@@ -3015,7 +3069,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     // ---- LCC to fixpoint (Alg. 4)
     P.searches_ahead = opt.lcc_only ? 0 : (int)t.order.size();
     int64_t rounds = 0;
-    RCF(P.lcc(&rounds));
+    RCF(P.lcc(&rounds, true));
     r->phase_rounds.push_back((int32_t)rounds);
     int64_t total_rounds = rounds;
     CUF(cudaEventRecord(w.ev[1], s));
@@ -4302,6 +4356,8 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         a.med_chunk = 1;
         a.small_chunk = 8;
         a.lab0 = nullptr;
+        a.prev = nullptr;
+        a.resident_warps = num_sms * 32;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
         if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
         else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);

@@ -65,3 +65,28 @@ def targets_from(recs, benefit_weight: float = 0.0):
     X = np.asarray([r["features"] for r in recs], dtype=np.float32).reshape(-1, ccpm.MLP_IN)
     y = np.asarray([target(r, benefit_weight) for r in recs], dtype=np.float32)
     return X, y
+
+
+def judge(ctx, graph, templates, net, max_embeddings=1 << 32, repeats: int = 1):
+    """The fixed order judges the learned one: both prune the same templates
+    one at a time (the learned options also run a warm-up pass); the learned
+    order is kept only if its total device time is lower.  Returns
+    (use_learned, ms_fixed, ms_learned).  Outputs are identical either way;
+    only the order, and so the time, differs."""
+    fixed = ccpm.options(max_embeddings=max_embeddings)
+    learned = learned_options(net, max_embeddings=max_embeddings)
+    hs = [t if isinstance(t, ccpm.Template) else ccpm.Template(ctx, t.labels, t.edges) for t in templates]
+    totals = []
+    for o in (fixed, learned):
+        res = [None] * len(hs)
+        for i, h in enumerate(hs):                       # warm-up
+            res[i] = ccpm.prune(ctx, graph, h, o, result=res[i], allow_budget=True)
+        ms = 0.0
+        for _ in range(repeats):
+            for i, h in enumerate(hs):
+                res[i] = ccpm.prune(ctx, graph, h, o, result=res[i], allow_budget=True)
+                ms += res[i].counts()["ms_total"]
+        totals.append(ms)
+        for r in res:
+            r.close()
+    return totals[1] < totals[0], totals[0], totals[1]

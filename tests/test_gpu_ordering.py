@@ -1,5 +1,7 @@
 """Learned constraint ordering: identical results, oracle-exact round counts
-for the order it chose, and the time it saves over the fixed order."""
+for the order it chose, and what it gains over the fixed order (reported as
+medians with interquartile ranges over repeats; no gain is asserted, since a
+gain within run-to-run noise is no gain; the fixed order then judges it)."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,7 @@ def test_learned_order_is_exact_and_reports_gain(ctx, capsys):
     assert X.shape[0] >= 80
     net = ordering.train(ctx, X, y, steps=800)
     evalset = random_templates(g, 12, 5000)
-    t_fixed = t_learned = 0.0
+    changed = 0
     for i, t in enumerate(evalset):
         h = ccpm.Template(ctx, t.labels, t.edges)
         fixed = ccpm.prune(ctx, graph, h, ccpm.options(), allow_budget=True)
@@ -47,8 +49,7 @@ def test_learned_order_is_exact_and_reports_gain(ctx, capsys):
         cf, cl = fixed.counts(), learned.counts()
         assert cf["match_embeddings"] == cl["match_embeddings"]
         assert sorted(learned.order()) == list(range(len(learned.order())))
-        t_fixed += cf["ms_total"]
-        t_learned += cl["ms_total"]
+        changed += learned.order() != fixed.order()
         if i < 4:
             # the oracle, given the same order, reproduces every phase's rounds
             K = cgen.generate(t.labels, t.edges)
@@ -56,6 +57,24 @@ def test_learned_order_is_exact_and_reports_gain(ctx, capsys):
                                constraints=[K[j] for j in learned.order()])
             assert learned.phase_rounds() == ref.phase_rounds
             np.testing.assert_array_equal(learned.omega(), ref.omega)
+    # what the network gains: totals over the evaluation templates, five
+    # interleaved repeats per order, median and interquartile range
+    hs = [ccpm.Template(ctx, t.labels, t.edges) for t in evalset]
+    tot = {"fixed": [], "learned": []}
+    for _ in range(5):
+        for name, o in (("fixed", ccpm.options()), ("learned", ordering.learned_options(net))):
+            ms = 0.0
+            for h in hs:
+                r = ccpm.prune(ctx, graph, h, o, allow_budget=True)
+                ms += r.counts()["ms_total"]
+                r.close()
+            tot[name].append(ms)
+    q = {k: np.percentile(v, [25, 50, 75]) for k, v in tot.items()}
+    gain = q["fixed"][1] / q["learned"][1]
     with capsys.disabled():
-        print(f"\nlearned order: {t_learned:.2f} ms vs fixed {t_fixed:.2f} ms "
-              f"({t_fixed / max(t_learned, 1e-9):.2f}x) over {len(evalset)} templates")
+        print(f"\nlearned order: median {q['learned'][1]:.2f} ms (IQR {q['learned'][0]:.2f}-{q['learned'][2]:.2f}) "
+              f"vs fixed {q['fixed'][1]:.2f} ms (IQR {q['fixed'][0]:.2f}-{q['fixed'][2]:.2f}): {gain:.3f}x over "
+              f"{len(evalset)} templates, order changed on {changed}")
+    # the judge keeps the learned order only when it is faster on its slice
+    use, ms_f, ms_l = ordering.judge(ctx, graph, evalset, net)
+    assert use == (ms_l < ms_f)
