@@ -513,6 +513,18 @@ def run_c4(args, cfg):
             for i, h in enumerate(hs):
                 res_plearn[i] = ccpm.prune(ctx, graph, h, always_learned, result=res_plearn[i], allow_budget=True)
         _, ms_plearn = timed(stream, plain_learned)
+        # ablation (Sec. 6.6): the plain pass again without edge elimination
+        abl = ccpm.options(max_embeddings=args.count_cap, no_edge_elimination=1)
+        res_abl = [None] * len(hs)
+
+        def plain_no_eta():
+            for i, h in enumerate(hs):
+                res_abl[i] = ccpm.prune(ctx, graph, h, abl, result=res_abl[i], allow_budget=True)
+        plain_no_eta()
+        _, ms_abl = timed(stream, plain_no_eta)
+        same_abl = same_results(res_plain, res_abl, g.n, words, dev)
+        for r in res_abl:
+            r.close()
         same = same_results(res_plain, res_batch, g.n, words, dev) and \
             same_results(res_plain, res_bfix, g.n, words, dev) and \
             same_results(res_plain, res_plearn, g.n, words, dev)
@@ -576,6 +588,10 @@ def run_c4(args, cfg):
             "batched_fixed_ms": ms_bfix, "plain_learned_ms": ms_plearn,
             "nlcc_ms_plain_fixed": nlcc_plain, "nlcc_ms_plain_learned": nlcc_plearn,
             "identical_outputs": bool(same),
+            "ablation_edge_elimination": {"plain_ms_without": ms_abl, "plain_ms_with": ms_plain,
+                                          "slowdown_without": ms_abl / ms_plain if ms_plain else None,
+                                          "identical_outputs": bool(same_abl),
+                                          "paper": "2-9x faster with edge elimination (Sec. 6.6, WDC-3)"},
             "tts_ms": {"median": statistics.median(tts), "max": max(tts), "sum": sum(tts)},
             "plain_split_ms": {k: sum(c[k] for c in counts_plain) for k in
                                ("ms_lcc", "ms_nlcc", "ms_final", "ms_final_count", "ms_final_vertex",

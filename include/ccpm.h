@@ -118,7 +118,10 @@ typedef struct {
     int      short_rows;           /* rows up to this many entries are walked 32   */
                                    /* rows per warp as one stream; longer ones a   */
                                    /* warp per row: 0 = library default (64)      */
-    int      reserved[2];
+    int      no_edge_elimination;  /* 1: ablation: LCC counts every live neighbour */
+                                   /* (no edge elimination by eta); ω*, E* and    */
+                                   /* the count are unchanged, only the time      */
+    int      reserved[1];
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 

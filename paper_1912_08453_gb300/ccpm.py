@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("max_embeddings", ctypes.c_uint64), ("search_budget", ctypes.c_uint64),
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
                 ("compact", ctypes.c_int), ("search_split", ctypes.c_int),
-                ("lcc_only", ctypes.c_int), ("short_rows", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+                ("lcc_only", ctypes.c_int), ("short_rows", ctypes.c_int), ("no_edge_elimination", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1),
                 ("mlp", ctypes.c_void_p)]
 
 

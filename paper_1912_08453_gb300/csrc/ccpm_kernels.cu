@@ -255,6 +255,8 @@ struct LccArgs {
     // previous round's counters, and a round after the fixpoint does nothing
     const RoundStats *prev;       // nullable: sizes are the fields above
     int resident_warps;           // warps of one resident wave (medium prefetch unit)
+    uint32_t eta_off;             // ~0: ablation without edge elimination (every live
+                                  // neighbour passes eta); 0: the method
 };
 
 template <int MAXC>
@@ -484,7 +486,7 @@ __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, 
         const int64_t b = b_nx;
         const int d = d_nx;
         v_nx = load_v(ch + stride);              // in flight during this batch
-        const uint32_t nbr = wv ? nbr_mask(wv, s) : 0u;
+        const uint32_t nbr = wv ? (nbr_mask(wv, s) | a.eta_off) : 0u;
         int S = d;                               // inclusive prefix of the row lengths
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -643,7 +645,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         const int64_t end = min(rend, beg + (int64_t)a.hub_deg);
         if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
-        scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
+        scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
                                    slm, cm);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
@@ -711,7 +713,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             if (wv) {
                 if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
-                scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s), a.col, a.om_cur, a.ebits, s, p, tl.scanned,
+                scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned,
                                            a.lab0, slm, cm);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
@@ -2410,6 +2412,7 @@ struct Pipeline {
     int64_t search_launches = 0, nlcc_entries = 0, item_passes = 0;
     int maxc = 0;
     int short_max = kSmallDeg;      // rows up to this length take the flat short-row path
+    bool eta_off = false;           // ablation: no edge elimination
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
     const int32_t *lcol = nullptr;
@@ -2447,24 +2450,28 @@ struct Pipeline {
 
     // One LCC round.  slot: its counters; prev (nullable): the previous
     // round's counters, from which the round reads its list sizes on the
-    // device (a round queued without a host round trip).
-    int launch_round(RoundStats *slot, const RoundStats *prev) {
+    // device (a round queued without a host round trip).  step: its place in
+    // the group of queued rounds; round `step` of a group reads the omega and
+    // list buffers the previous one wrote (the host flips cur / li only once
+    // the group is done, by the number of rounds that ran).
+    int launch_round(RoundStats *slot, const RoundStats *prev, int step = 0) {
         Workspace &w = ctx->ws;
+        const int c = cur ^ (step & 1), l = li ^ (step & 1);
         LccArgs a;
         a.rp = lrp;
         a.col = lcol;
-        a.om_cur = w.om[cur];
-        a.om_next = w.om[cur ^ 1];
+        a.om_cur = w.om[c];
+        a.om_next = w.om[c ^ 1];
         a.ebits = lbits;
-        a.small_in = w.small[li];
-        a.med_in = w.med[li];
-        a.chunk_in = w.chunk[li];
+        a.small_in = w.small[l];
+        a.med_in = w.med[l];
+        a.chunk_in = w.chunk[l];
         a.n_small = n_small;
         a.n_med = n_med;
         a.n_chunk = n_chunk;
-        a.small_out = w.small[li ^ 1];
-        a.med_out = w.med[li ^ 1];
-        a.chunk_out = w.chunk[li ^ 1];
+        a.small_out = w.small[l ^ 1];
+        a.med_out = w.med[l ^ 1];
+        a.chunk_out = w.chunk[l ^ 1];
         a.acc = w.acc;
         a.st = slot;
         a.prev = prev;
@@ -2473,6 +2480,7 @@ struct Pipeline {
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
         a.lab0 = from_labels ? g->lab : nullptr;
         a.lmask = lm0;
+        a.eta_off = eta_off ? ~0u : 0u;
         from_labels = false;
         // prefetch units: large enough to hide the per-vertex loads, small
         // enough that every resident warp gets several of them
@@ -2517,7 +2525,7 @@ struct Pipeline {
             CU(ctx, cudaMemsetAsync(w.st_ring, 0, sizeof(RoundStats) * (size_t)G, ctx->stream));
             CU(ctx, cudaEventRecord(w.ev[4], ctx->stream));
             for (int i = 0; i < G; i++) {
-                int rc = launch_round(w.st_ring + i, i ? w.st_ring + i - 1 : nullptr);
+                int rc = launch_round(w.st_ring + i, i ? w.st_ring + i - 1 : nullptr, i);
                 if (rc) return rc;
             }
             CU(ctx, cudaEventRecord(w.ev[5], ctx->stream));
@@ -2995,6 +3003,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.lcol = g->col;
     P.lbits = w.ebits;
     P.short_max = opt.short_rows > 0 ? std::min(opt.short_rows, kMaxHubDeg) : kSmallDeg;
+    P.eta_off = opt.no_edge_elimination != 0;
     g->prunes++;
     P.compact_mode = opt.compact;
     cudaStream_t s = ctx->stream;
@@ -4358,6 +4367,7 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         a.lab0 = nullptr;
         a.prev = nullptr;
         a.resident_warps = num_sms * 32;
+        a.eta_off = 0u;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
         if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
         else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);

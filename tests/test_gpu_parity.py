@@ -243,3 +243,19 @@ def test_count_cap_keeps_exact_sets(ctx):
     np.testing.assert_array_equal(gpu["omega"], ref.omega)
     np.testing.assert_array_equal(gpu["ebits"], ref.ebits)
     np.testing.assert_array_equal(ref.omega, ref_full.omega)
+
+
+def test_edge_elimination_ablation_keeps_the_result(ctx):
+    # options.no_edge_elimination: LCC counts every live neighbour, so its
+    # fixpoint is larger (more rounds of work later), but the final exact
+    # search gives the same omega*, E* and count as the method (Sec. 6.6's
+    # ablation measures only the time)
+    g = wl.rmat_graph(14, seed=10)
+    pool = [L for L in wl.labels_by_frequency(g) if L > 0][:6]
+    base = wl.Template([5, 4, 8, 7, 4, 5], [(0, 1), (1, 2), (1, 3), (3, 4), (3, 5), (2, 3)])
+    for t in [base] + wl.edit_variants(base, 5, seed=9, label_pool=pool, n_min=4, n_max=8):
+        on = gpu_run(ctx, g, t.labels, t.edges)
+        off = gpu_run(ctx, g, t.labels, t.edges, no_edge_elimination=1)
+        np.testing.assert_array_equal(on["omega"], off["omega"])
+        np.testing.assert_array_equal(on["ebits"], off["ebits"])
+        assert on["counts"]["match_embeddings"] == off["counts"]["match_embeddings"]
