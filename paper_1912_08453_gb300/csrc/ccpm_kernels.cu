@@ -1191,6 +1191,11 @@ struct WarpSearch {
     int jc_level;
     int jc_len[2];
     int32_t jc[2][128];
+    // the last match this warp marked (by plan position) and its plan: a
+    // match found next in depth-first order usually differs from it only at
+    // its last positions, and only what differs needs marking
+    const DevPlan *last_plan;
+    int32_t last[kMaxT];
 };
 constexpr int kJoinCache = 2, kJoinCacheLen = 128;
 
@@ -1393,6 +1398,42 @@ __device__ __forceinline__ void mark_vertices(const SearchArgs &a, const DevPlan
     __syncwarp();
 }
 
+// Mark a match found by a marking enumeration: every (vertex, template
+// vertex) pair and both entries of every template edge, skipping those the
+// warp's previous match (same plan) already marked: marks are only ever set,
+// so a pair or an edge whose positions hold the same vertices as in that
+// match is marked already.
+__device__ __forceinline__ void mark_match(const SearchArgs &a, const DevPlan &P, WarpSearch &W) {
+    const int lane = (int)lane_id();
+    const bool same_plan = W.last_plan == &P;
+    if (lane < P.k) {
+        const int32_t x = W.psi[lane];
+        if (!(same_plan && W.last[lane] == x)) {
+            const uint32_t bit = 1u << P.q[lane];
+            if (!(a.om_out[x] & bit)) atomicOr(&a.om_out[x], bit);
+        }
+    }
+    for (int t = lane; t < P.n_marks; t += 32) {
+        const int pa = P.mark_a[t], pb = P.mark_b[t];
+        const int32_t x = W.psi[pa], y = W.psi[pb];
+        if (same_plan && W.last[pa] == x && W.last[pb] == y) continue;
+        const int64_t e1 = find_entry(a.rp, a.col, x, y);
+        const int64_t e2 = find_entry(a.rp, a.col, y, x);
+        if (e1 >= 0) {
+            const uint32_t b1 = 1u << (uint32_t)(e1 & 31);
+            if (!(a.eb_out[e1 >> 5] & b1)) atomicOr(&a.eb_out[e1 >> 5], b1);
+        }
+        if (e2 >= 0) {
+            const uint32_t b2 = 1u << (uint32_t)(e2 & 31);
+            if (!(a.eb_out[e2 >> 5] & b2)) atomicOr(&a.eb_out[e2 >> 5], b2);
+        }
+    }
+    __syncwarp();
+    if (lane < P.k) W.last[lane] = W.psi[lane];
+    if (lane == 0) W.last_plan = &P;
+    __syncwarp();
+}
+
 // Search modes: does an embedding exist / count the embeddings / count them
 // and mark the vertices and edges of every one / count them and list them.
 constexpr int kExist = 0, kCount = 1, kMark = 2, kList = 3;
@@ -1475,7 +1516,7 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
     if (d0 >= k) {                                  // the placed prefix is already a full map
         if (MODE == kExist) return true;
         matches++;
-        if (MODE == kMark) { mark_vertices(a, P, W); mark_edges(a, P, W); }
+        if (MODE == kMark) mark_match(a, P, W);
         if (MODE == kList) list_embedding(a, P, W);
         return false;
     }
@@ -1526,12 +1567,8 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
         if (d == k - 1) {
             if (MODE == kExist) return true;
             matches++;                              // kMark / kList (counting never stores last-level masks)
-            if (MODE == kList) {
-                list_embedding(a, P, W);
-            } else {
-                mark_vertices(a, P, W);
-                mark_edges(a, P, W);
-            }
+            if (MODE == kList) list_embedding(a, P, W);
+            else mark_match(a, P, W);
             continue;
         }
         d++;
@@ -1582,6 +1619,8 @@ k_final_search(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
+    if (lane == 0) W.last_plan = nullptr;
+    __syncwarp();
     unsigned long long entries = 0, matches = 0;
     bool over = false;
     for (int64_t it = grab_root(a); it < a.n_roots; it = grab_root(a)) {
@@ -1768,6 +1807,8 @@ k_final_items(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
+    if (lane == 0) W.last_plan = nullptr;
+    __syncwarp();
     unsigned long long entries = 0, matches = 0;
     bool over = false;
     for (int64_t it0 = grab_items(a, kItemBatch); it0 < a.n_items; it0 = grab_items(a, kItemBatch)) {
