@@ -479,9 +479,9 @@ def run_c4(args, cfg):
         t_train = time.time()
         net = ordering.train(ctx, X, y, steps=2000) if len(recs) >= 8 else None
         train_s = time.time() - t_train
-        # the fixed order judges the learned one on a slice of this batch
-        # (plain, one template at a time); the batch keeps it only if it wins
-        use_learned, judge_fixed, judge_learned = (ordering.judge(ctx, graph, hs[:16], net, args.count_cap)
+        # the fixed order decides on a slice of this batch whether the learned
+        # one is used (plain, one template at a time): only if it is faster
+        use_learned, check_fixed, check_learned = (ordering.choose(ctx, graph, hs[:16], net, args.count_cap)
                                                    if net else (False, 0.0, 0.0))
         learned = ordering.learned_options(net, max_embeddings=args.count_cap) if use_learned else cap
         res_batch = ccpm.prune_batch(ctx, graph, hs, learned, allow_budget=True)   # autotunes the workers
@@ -594,6 +594,7 @@ def run_c4(args, cfg):
                        "l2": "inputs larger than L2 (2.1 GB column array), no flush",
                        "parallelism": f"templates dealt over {world} ranks" if world > 1 else "one GPU"},
             "plain_ms": ms_plain, "batched_learned_ms": total_ms / args.steps,
+            "batched_step_ms": t_batch,
             "speedup": ms_plain / (total_ms / args.steps) if total_ms > 0 else None,
             "batched_fixed_ms": ms_bfix, "plain_learned_ms": ms_plearn,
             "nlcc_ms_plain_fixed": nlcc_plain, "nlcc_ms_plain_learned": nlcc_plearn,
@@ -609,9 +610,9 @@ def run_c4(args, cfg):
             "counts_valid": int(sum(c["count_valid"] for c in counts_plain)),
             "autotune": workers,
             "training_records": len(recs), "training_s": train_s, "graph_gen_s": gen_s,
-            "learned_order": {"used_in_batch": bool(use_learned), "judge_slice_ms_fixed": judge_fixed,
-                              "judge_slice_ms_learned": judge_learned,
-                              "note": "the fixed order judges the learned one on the first 16 templates; "
+            "learned_order": {"used_in_batch": bool(use_learned), "check_slice_ms_fixed": check_fixed,
+                              "check_slice_ms_learned": check_learned,
+                              "note": "the learned order is used only if faster than the fixed one on the first 16 templates; "
                                       "plain_learned_ms always uses the learned order"},
             "search_entries_per_s": search_entries / (total_ms / 1e3) if total_ms > 0 else 0.0,
             "roofline": dominant, "rooflines": [roof_lcc, roof_search],

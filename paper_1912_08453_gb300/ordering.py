@@ -67,8 +67,8 @@ def targets_from(recs, benefit_weight: float = 0.0):
     return X, y
 
 
-def judge(ctx, graph, templates, net, max_embeddings=1 << 32, repeats: int = 1):
-    """The fixed order judges the learned one: both prune the same templates
+def choose(ctx, graph, templates, net, max_embeddings=1 << 32, repeats: int = 1):
+    """The fixed order decides whether the learned one is used: both prune the same templates
     one at a time (the learned options also run a warm-up pass); the learned
     order is kept only if its total device time is lower.  Returns
     (use_learned, ms_fixed, ms_learned).  Outputs are identical either way;

@@ -1,7 +1,7 @@
 """Learned constraint ordering: identical results, oracle-exact round counts
 for the order it chose, and what it gains over the fixed order (reported as
 medians with interquartile ranges over repeats; no gain is asserted, since a
-gain within run-to-run noise is no gain; the fixed order then judges it)."""
+gain within run-to-run noise is no gain; the fixed order then decides)."""
 import numpy as np
 import pytest
 
@@ -75,6 +75,6 @@ def test_learned_order_is_exact_and_reports_gain(ctx, capsys):
         print(f"\nlearned order: median {q['learned'][1]:.2f} ms (IQR {q['learned'][0]:.2f}-{q['learned'][2]:.2f}) "
               f"vs fixed {q['fixed'][1]:.2f} ms (IQR {q['fixed'][0]:.2f}-{q['fixed'][2]:.2f}): {gain:.3f}x over "
               f"{len(evalset)} templates, order changed on {changed}")
-    # the judge keeps the learned order only when it is faster on its slice
-    use, ms_f, ms_l = ordering.judge(ctx, graph, evalset, net)
+    # the learned order is chosen only when it is faster on the checked slice
+    use, ms_f, ms_l = ordering.choose(ctx, graph, evalset, net)
     assert use == (ms_l < ms_f)

@@ -524,9 +524,9 @@ def test_edge_only_change_counts_a_round():
     change (Alg. 4 sets the change flag for eliminated edges): 2 rounds.
 
     Template q0 (label 0) - q1 (label 1).  Background: a (0) - b (1) and
-    a (0) - c (0).  Round 1: the entry a-c is not compatible (no template
+    a (0) - c (0).  First LCC round: the entry a-c is not compatible (no template
     edge joins q0 to q0) and is removed; a keeps q0 through b, b keeps q1,
-    c has no compatible neighbour and dies.  Round 2 changes nothing."""
+    c has no compatible neighbour and dies.  The second round changes nothing."""
     g = wl.graph_from_edge_list(3, [(0, 1), (0, 2)], [0, 1, 0])
     og = oracle.Graph(g.row_ptr, g.col, g.labels)
     tl, te = [0, 1], [(0, 1)]
