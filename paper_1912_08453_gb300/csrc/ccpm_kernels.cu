@@ -257,7 +257,28 @@ struct LccArgs {
     int resident_warps;           // warps of one resident wave (medium prefetch unit)
     uint32_t eta_off;             // ~0: ablation without edge elimination (every live
                                   // neighbour passes eta); 0: the method
+    // a narrow copy of omega for the neighbour gathers (templates of at most
+    // 8 / 16 vertices: 1 / 2 bytes per vertex, 4x / 2x fewer bytes than the
+    // 32-bit words, so it stays in L2 at scale 25): read nw_cur, written to
+    // nw_next beside om_next; nw_bytes 0 = no copy (gather om_cur)
+    const void *nw_cur;
+    void *nw_next;
+    int nw_bytes;
 };
+
+// A neighbour's omega for the LCC gathers: from the narrow copy when there is one.
+__device__ __forceinline__ uint32_t gather_om(const uint32_t *__restrict__ om, const void *nw, int nwb, int32_t u) {
+    if (nwb == 1) return __ldg((const uint8_t *)nw + u);
+    if (nwb == 2) return __ldg((const uint16_t *)nw + u);
+    return __ldg(om + u);
+}
+
+// omega'(v) of the next round, and its narrow copy.
+__device__ __forceinline__ void store_om(const LccArgs &a, int32_t v, uint32_t w) {
+    a.om_next[v] = w;
+    if (a.nw_bytes == 1) ((uint8_t *)a.nw_next)[v] = (uint8_t)w;
+    else if (a.nw_bytes == 2) ((uint16_t *)a.nw_next)[v] = (uint16_t)w;
+}
 
 template <int MAXC>
 struct Partial {
@@ -289,7 +310,8 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const uint32_t *__restrict__ om, uint32_t *ebits,
                                               const SmemTmpl &s, Partial<MAXC> &p,
                                               uint32_t &scanned, const uint8_t *__restrict__ lab0,
-                                              const uint32_t *slm, const uint32_t (&cm)[4]) {
+                                              const uint32_t *slm, const uint32_t (&cm)[4], const void *nw,
+                                              int nwb) {
     constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
     const int64_t w0 = beg >> 5;
@@ -326,7 +348,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
         for (int j = 0; j < UNR; j++) {
             was[j] = act[j];
             if (lab0) wu[j] = act[j] ? slm[__ldg(lab0 + u[j])] : 0u;
-            else wu[j] = act[j] ? __ldg(om + u[j]) : 0u;
+            else wu[j] = act[j] ? gather_om(om, nw, nwb, u[j]) : 0u;
         }
         if (k0 + UNR < nwin) load_step(k0 + UNR);
 #pragma unroll
@@ -507,7 +529,7 @@ __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, 
         load_row();                              // the next batch's omegas and offsets
         for (int k0 = 0; k0 < T; k0 += 32) {
             uint32_t w = 0u;
-            if (cur.act) w = a.lab0 ? slm[__ldg(a.lab0 + cur.u)] : __ldg(a.om_cur + cur.u);
+            if (cur.act) w = a.lab0 ? slm[__ldg(a.lab0 + cur.u)] : gather_om(a.om_cur, a.nw_cur, a.nw_bytes, cur.u);
             ShortStep nx;
             if (k0 + 32 < T) short_locate<DENSE>(a, sr, k0 + 32, T, start, d, nx);
             const bool keep = (w & cur.nb) != 0u;
@@ -579,7 +601,7 @@ __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, 
                 if (keep != wv) tl.changed = 1u;
                 if (keep == 0u) clear_row<1>(a.ebits, b, b + d, 0);
             }
-            a.om_next[v] = keep;
+            store_om(a, v, keep);
             if (a.deg) a.deg[v] = keep ? (int64_t)N : 0;
         }
         // the batch's vertices that were active at the start of the round
@@ -635,7 +657,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         const uint32_t wv = __ldg(a.om_cur + ci.v);
         if (wv == 0u) {
             if (ci.c == 0 && lane == 0) {
-                a.om_next[ci.v] = 0u;
+                store_om(a, ci.v, 0u);
                 if (a.deg) a.deg[ci.v] = 0;
             }
             continue;
@@ -646,7 +668,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
         scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
-                                   slm, cm);
+                                   slm, cm, a.nw_cur, a.nw_bytes);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -675,7 +697,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
             for (int c = 0; c < MAXC; c++) tot.cnt[c] = atomicAdd(&h->cnt[c], 0u);
             uint32_t keep = decide<MAXC>(wv, tot, s);
             if (lane == 0) {
-                a.om_next[ci.v] = keep;
+                store_om(a, ci.v, keep);
                 if (a.deg) a.deg[ci.v] = keep ? (int64_t)tot.nN : 0;
             }
             if (lane == 0 && keep) { tl.kept += tot.nN; tl.rows_next += (unsigned long long)(rend - rbeg); }
@@ -714,7 +736,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
                 scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned,
-                                           a.lab0, slm, cm);
+                                           a.lab0, slm, cm, a.nw_cur, a.nw_bytes);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
                 p.achg = grp_or<32>(p.achg);
@@ -727,7 +749,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 if (keep == 0u) clear_row<32>(a.ebits, beg, end, lane);
             }
             if (lane == 0) {
-                a.om_next[v] = keep;
+                store_om(a, v, keep);
                 if (a.deg) a.deg[v] = keep ? (int64_t)p_nN : 0;
             }
         }
@@ -2018,6 +2040,23 @@ k_materialize(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restr
     }
 }
 
+// Both narrow copies of omega from the current omega (an LCC phase starts
+// with the two omega buffers equal).
+__global__ void __launch_bounds__(256)
+k_narrow(int64_t n, const uint32_t *__restrict__ om, void *nw0, void *nw1, int bytes) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t w = om[v];
+        if (bytes == 1) {
+            ((uint8_t *)nw0)[v] = (uint8_t)w;
+            ((uint8_t *)nw1)[v] = (uint8_t)w;
+        } else {
+            ((uint16_t *)nw0)[v] = (uint16_t)w;
+            ((uint16_t *)nw1)[v] = (uint16_t)w;
+        }
+    }
+}
+
 __global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
 __global__ void k_and_word(uint32_t *p, uint32_t v) { *p &= v; }
 
@@ -2076,6 +2115,7 @@ struct Workspace {
     int64_t n = 0, m = 0, words = 0;
     int hub_deg = 0;
     uint32_t *om[2] = {nullptr, nullptr};
+    uint16_t *nw[2] = {nullptr, nullptr};   // narrow copies of omega (up to 16 template vertices)
     uint32_t *ebits = nullptr;
     int32_t *small[2] = {nullptr, nullptr};
     int32_t *med[2] = {nullptr, nullptr};
@@ -2215,7 +2255,7 @@ int dalloc(ccpm_ctx *ctx, T **p, size_t count) {
 }
 
 void ws_free(Workspace &w) {
-    cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.ebits);
+    cudaFree(w.om[0]); cudaFree(w.om[1]); cudaFree(w.nw[0]); cudaFree(w.nw[1]); cudaFree(w.ebits);
     cudaFree(w.small[0]); cudaFree(w.small[1]); cudaFree(w.med[0]); cudaFree(w.med[1]);
     cudaFree(w.chunk[0]); cudaFree(w.chunk[1]); cudaFree(w.acc); cudaFree(w.roots);
     cudaFree(w.sat); cudaFree(w.items); cudaFree(w.items2); cudaFree(w.spill_items); cudaFree(w.plans); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.next_root);
@@ -2248,6 +2288,8 @@ int ws_ensure(ccpm_ctx *ctx, ccpm_graph *g, int hub_deg) {
     int rc;
     if ((rc = dalloc(ctx, &w.om[0], (size_t)g->n))) return rc;
     if ((rc = dalloc(ctx, &w.om[1], (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.nw[0], (size_t)g->n))) return rc;
+    if ((rc = dalloc(ctx, &w.nw[1], (size_t)g->n))) return rc;
     if ((rc = dalloc(ctx, &w.ebits, (size_t)w.words + 1))) return rc;
     for (int i = 0; i < 2; i++) {
         if ((rc = dalloc(ctx, &w.small[i], (size_t)g->n))) return rc;
@@ -2454,6 +2496,7 @@ struct Pipeline {
     int maxc = 0;
     int short_max = kSmallDeg;      // rows up to this length take the flat short-row path
     bool eta_off = false;           // ablation: no edge elimination
+    int nw_bytes = 0;               // width of the narrow copy of omega (0: none)
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
     const int32_t *lcol = nullptr;
@@ -2522,6 +2565,9 @@ struct Pipeline {
         a.lab0 = from_labels ? g->lab : nullptr;
         a.lmask = lm0;
         a.eta_off = eta_off ? ~0u : 0u;
+        a.nw_bytes = nw_bytes;
+        a.nw_cur = w.nw[c];
+        a.nw_next = w.nw[c ^ 1];
         from_labels = false;
         // prefetch units: large enough to hide the per-vertex loads, small
         // enough that every resident warp gets several of them
@@ -2559,6 +2605,11 @@ struct Pipeline {
     int lcc(int64_t *rounds, bool first_alone = false) {
         Workspace &w = ctx->ws;
         int64_t r = 0;
+        if (nw_bytes) {
+            launches++;
+            k_narrow<<<grid_for(ctx, g->n, 256, 8), 256, 0, ctx->stream>>>(g->n, w.om[cur], w.nw[0], w.nw[1], nw_bytes);
+            CU(ctx, cudaGetLastError());
+        }
         bool alone = first_alone;
         for (;;) {
             const int G = alone ? 1 : kLccGroup;
@@ -3045,6 +3096,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.lbits = w.ebits;
     P.short_max = opt.short_rows > 0 ? std::min(opt.short_rows, kMaxHubDeg) : kSmallDeg;
     P.eta_off = opt.no_edge_elimination != 0;
+    P.nw_bytes = t.n0 <= 8 ? 1 : (t.n0 <= 16 ? 2 : 0);
     g->prunes++;
     P.compact_mode = opt.compact;
     cudaStream_t s = ctx->stream;
@@ -4409,6 +4461,9 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         a.prev = nullptr;
         a.resident_warps = num_sms * 32;
         a.eta_off = 0u;
+        a.nw_bytes = 0;
+        a.nw_cur = nullptr;
+        a.nw_next = nullptr;
         const int g = grid((n_chunk + n_med + (n_small + 7) / 8) * 32, 256);
         if (dt.n_cls == 0) k_lcc_round<0, false><<<g, 256, 0, s>>>(a, dt);
         else if (dt.n_cls <= 4) k_lcc_round<4, false><<<g, 256, 0, s>>>(a, dt);
