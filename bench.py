@@ -107,6 +107,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the C2/C3 lines inside the C4 run")
+    p.add_argument("--plain-only", action="store_true",
+                   help="C4: one plain pass over the batch and nothing else (a profiler's command)")
     p.add_argument("--count-cap", type=int, default=1 << 16,
                    help="matches counted per template before the count is reported invalid "
                         "(omega* and E* stay exact; every C4 template has more than 2^20 matches)")
@@ -254,12 +256,16 @@ def lcc_first_round(counts):
 def search_roofline(counts, workload):
     """The search kernels (NLCC walks and the final template-driven search):
     8 algorithmic bytes per row entry examined (column index and the
-    neighbour's omega); no pass mark (random, combinatorial access)."""
+    neighbour's omega); no pass mark (random, combinatorial access).  One
+    'launch' here is the search work of one template's prune (the device
+    time of its NLCC search passes plus its whole final step), and traffic
+    is counted the same way."""
     ent = sum(c["edges_scanned_search"] for c in counts)
     ms = sum(c["ms_search_kernel"] + c["ms_final"] for c in counts)
-    return roofline("k_nlcc_items/k_final_items/k_edge_search", 8 * ent, ms,
-                    sum(c["search_launches"] for c in counts), workload,
-                    {"entries": ent, "note": "device time of the NLCC search kernels plus the whole final step"})
+    return roofline("search kernels per template", 8 * ent, ms, len(counts), workload,
+                    {"entries": ent, "note": "per template: k_nlcc_items, k_expand*, k_final_items, k_edge_items, "
+                                             "k_edge_search; device time of the NLCC search passes plus the whole "
+                                             "final step"})
 
 
 def cpu_oracle(g_host, templates, parallel):
@@ -423,11 +429,12 @@ def single_template_line(args, cfg, ctx, stream, local, reps=2):
             c = cs[-1]
             out["templates"][name + "_lcc_phase"] = {
                 "lcc_ms": dt, "rounds": r.phase_rounds(), "active_v_fixpoint": c["active_v"],
-                "lcc_first_round": lcc_first_round([c]), "lcc_roofline": lcc_roofline([c], cfg["name"])}
+                "lcc_first_round": lcc_first_round([c]),
+                "lcc_roofline": lcc_roofline([c], cfg["name"] + "-lcc-phase")}
             r.close()
             t.close()
     if lcc_counts:
-        out["lcc_phase_roofline"] = lcc_roofline(lcc_counts, cfg["name"])
+        out["lcc_phase_roofline"] = lcc_roofline(lcc_counts, cfg["name"] + "-lcc-phase")
         out["lcc_phase_first_round"] = lcc_first_round(lcc_counts)
     graph.close()
     del g
@@ -805,10 +812,40 @@ def main():
     if args.impl == "reference":
         run_reference(args, cfg)
         return
+    if "base" in cfg and args.plain_only:
+        run_c4_plain_pass(args, cfg)
+        return
     if "base" in cfg:
         run_c4(args, cfg)
         return
     run_single(args, cfg)
+
+
+def run_c4_plain_pass(args, cfg):
+    """One plain pass over the batch (one template at a time, fixed order):
+    the command the search kernels' DRAM counters are taken on, so that they
+    divide by exactly the templates of one pass."""
+    import torch
+    from paper_1912_08453_gb300.build import build
+    from paper_1912_08453_gb300 import ccpm
+    build()
+    g = make_graph(cfg, device="cuda:0")
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    ctx = ccpm.Context(0, stream=stream.cuda_stream)
+    graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
+    cap = ccpm.options(max_embeddings=args.count_cap)
+    hs = [ccpm.Template(ctx, t.labels, t.edges) for t in batch_templates(cfg)]
+    with torch.cuda.stream(stream):
+        res = []
+        for h in hs:
+            res.append(ccpm.prune(ctx, graph, h, cap, allow_budget=True))
+    counts = [r.counts() for r in res]
+    print(json.dumps({"workload": cfg["name"] + "-plain-pass", "templates": len(hs),
+                      "search_entries": sum(c["edges_scanned_search"] for c in counts),
+                      "search_device_ms": sum(c["ms_search_kernel"] + c["ms_final"] for c in counts),
+                      "lcc_launches": sum(c["lcc_launches"] for c in counts),
+                      "lcc_alg_bytes": sum(c["lcc_alg_bytes"] for c in counts)}), flush=True)
 
 
 def run_single(args, cfg):
