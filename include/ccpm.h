@@ -121,7 +121,11 @@ typedef struct {
     int      no_edge_elimination;  /* 1: ablation: LCC counts every live neighbour */
                                    /* (no edge elimination by eta); ω*, E* and    */
                                    /* the count are unchanged, only the time      */
-    int      reserved[1];
+    int      entry_labels;         /* first LCC round reads a per-graph copy of the */
+                                   /* neighbour labels in entry order (1 byte per  */
+                                   /* entry, built once): 0 = when the initially   */
+                                   /* active rows hold >= 1/8 of the entries and   */
+                                   /* >= 2^22, 1 = always, -1 = never; same result */
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
                 ("compact", ctypes.c_int), ("search_split", ctypes.c_int),
                 ("lcc_only", ctypes.c_int), ("short_rows", ctypes.c_int), ("no_edge_elimination", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1),
+                ("entry_labels", ctypes.c_int),
                 ("mlp", ctypes.c_void_p)]
 
 

@@ -15,6 +15,7 @@ constexpr int kMaxCls = 32;         // label-multiplicity classes per template
 constexpr int kSmallDeg = 64;       // rows up to this length: the flat short-row path
 constexpr int kDefaultHubDeg = 1024;// longer rows are split into chunks of this size
 constexpr int kMaxHubDeg = 1 << 24; // larger hub_degree options are clamped to this
+constexpr int64_t kEntryLabelRows = (int64_t)1 << 22;   // first-round rows that pay for the entry labels
 constexpr uint64_t kDefaultSearchBudget = 1ull << 22;
 
 // Template tables for the LCC kernels.  A "class" is (q, L) with

@@ -195,6 +195,7 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
     WarpBuf<int32_t> bm{sbuf[1][wib], &scnt[1][wib], med_out, &st->n_med};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_pad = (n + 31) & ~(int64_t)31;
+    unsigned long long rows = 0;          // entries in the rows of the active vertices
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_pad; v += stride) {
         uint32_t w = 0;
         int64_t deg = 0;
@@ -205,6 +206,7 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
             om1[v] = w;
             if (w) deg = rp[v + 1] - rp[v];
         }
+        rows += (unsigned long long)deg;
         // buckets: short rows (4 lanes each), medium rows (a warp each), long
         // rows (split into pieces of hub_deg entries); every active vertex is
         // in exactly one of them
@@ -221,6 +223,8 @@ k_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ la
     }
     bs.flush();
     bm.flush();
+    for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(FULL_MASK, rows, o);
+    if (lane_id() == 0 && rows) atomicAdd(&st->row_entries, rows);
 }
 
 // -------------------------------------------------------------------------
@@ -251,6 +255,10 @@ struct LccArgs {
     // 4-byte omega word (lab0 = labels, lmask = label -> initial omega)
     const uint8_t *lab0;
     LabelMask lmask;
+    // with lab0: the neighbours' labels in CSR entry order (one byte per
+    // entry, built once per graph), so the first round reads neither the
+    // column index nor the neighbour's label: omega(u) = lmask[elab[e]]
+    const uint8_t *elab;
     // rounds queued without a host round trip: the list sizes come from the
     // previous round's counters, and a round after the fixpoint does nothing
     const RoundStats *prev;       // nullable: sizes are the fields above
@@ -311,7 +319,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const SmemTmpl &s, Partial<MAXC> &p,
                                               uint32_t &scanned, const uint8_t *__restrict__ lab0,
                                               const uint32_t *slm, const uint32_t (&cm)[4], const void *nw,
-                                              int nwb) {
+                                              int nwb, const uint8_t *__restrict__ elab) {
     constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
     const int64_t w0 = beg >> 5;
@@ -319,6 +327,7 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
     const int lo = (int)(beg - (w0 << 5));          // entries before lo belong to the previous row
     const int hi = (int)(end - (w0 << 5));          // entries from hi on belong to the next row
     const int32_t *cb = col + (w0 << 5) + lane;
+    const uint8_t *lb = (DENSE && elab) ? elab + (w0 << 5) + lane : nullptr;   // first round only
     uint32_t *eb = ebits + w0;
     // the column indices of the next step are loaded while the neighbour
     // omegas of the current step are gathered
@@ -337,7 +346,9 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
         for (int j = 0; j < UNR; j++) {
             const int rel = rel0 + j * 32;
             act[j] = rel >= lo && rel < hi && ((word[j] >> lane) & 1u);
-            u[j] = act[j] ? __ldcs(c0 + j * 32) : 0;
+            // the column index, or the neighbour's label when the entry labels are given
+            if (lb) u[j] = act[j] ? (int32_t)__ldcs(lb + k0 * 32 + j * 32) : 0;
+            else u[j] = act[j] ? __ldcs(c0 + j * 32) : 0;
         }
     };
     load_step(0);
@@ -347,7 +358,8 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
             was[j] = act[j];
-            if (lab0) wu[j] = act[j] ? slm[__ldg(lab0 + u[j])] : 0u;
+            if (lb) wu[j] = act[j] ? slm[u[j]] : 0u;
+            else if (lab0) wu[j] = act[j] ? slm[__ldg(lab0 + u[j])] : 0u;
             else wu[j] = act[j] ? gather_om(om, nw, nwb, u[j]) : 0u;
         }
         if (k0 + UNR < nwin) load_step(k0 + UNR);
@@ -473,7 +485,8 @@ __device__ __forceinline__ void short_locate(const LccArgs &a, ShortRows &sr, in
     st.nb = sr.nbr[r];
     st.act = valid;
     if (!DENSE && valid) st.act = (__ldg(a.ebits + (st.e >> 5)) >> (uint32_t)(st.e & 31)) & 1u;
-    st.u = st.act ? __ldcs(a.col + st.e) : 0;
+    if (DENSE && a.elab) st.u = st.act ? (int32_t)__ldcs(a.elab + st.e) : 0;   // the neighbour's label
+    else st.u = st.act ? __ldcs(a.col + st.e) : 0;
     __syncwarp();                                // sr.row is rewritten by the next step
 }
 
@@ -529,7 +542,9 @@ __device__ __forceinline__ void short_rows(const LccArgs &a, const SmemTmpl &s, 
         load_row();                              // the next batch's omegas and offsets
         for (int k0 = 0; k0 < T; k0 += 32) {
             uint32_t w = 0u;
-            if (cur.act) w = a.lab0 ? slm[__ldg(a.lab0 + cur.u)] : gather_om(a.om_cur, a.nw_cur, a.nw_bytes, cur.u);
+            if (cur.act)
+                w = (DENSE && a.elab) ? slm[cur.u]
+                           : (a.lab0 ? slm[__ldg(a.lab0 + cur.u)] : gather_om(a.om_cur, a.nw_cur, a.nw_bytes, cur.u));
             ShortStep nx;
             if (k0 + 32 < T) short_locate<DENSE>(a, sr, k0 + 32, T, start, d, nx);
             const bool keep = (w & cur.nb) != 0u;
@@ -668,7 +683,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
         scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
-                                   slm, cm, a.nw_cur, a.nw_bytes);
+                                   slm, cm, a.nw_cur, a.nw_bytes, a.elab);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -736,7 +751,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
                 scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned,
-                                           a.lab0, slm, cm, a.nw_cur, a.nw_bytes);
+                                           a.lab0, slm, cm, a.nw_cur, a.nw_bytes, a.elab);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
                 p.achg = grp_or<32>(p.achg);
@@ -1127,6 +1142,16 @@ k_materialize_fix(int64_t n, const uint32_t *__restrict__ om, const int64_t *__r
             if (dm && lane == 0) atomicAnd(&ebits[w0], ~dm);
         }
     }
+}
+
+// Zero the rows of the inactive vertices (one thread per vertex; the rows of
+// vertices that were never active, or that a non-local check emptied, still
+// carry bits the rounds never read).
+__global__ void __launch_bounds__(256)
+k_clear_dead_rows(int64_t n, const uint32_t *__restrict__ om, const int64_t *__restrict__ rp, uint32_t *ebits) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (om[v] == 0u) clear_row<1>(ebits, rp[v], rp[v + 1], 0);
 }
 
 // -------------------------------------------------------------------------
@@ -2186,6 +2211,7 @@ struct ccpm_graph {
     double tuned_ms = 0.0;        // the chosen setting's time on the tuning slice
     std::atomic<int> prunes{0};   // prunes started on this graph
     std::atomic<bool> lrows_ready{false};   // lcol/nlab built (read without the lock)
+    uint8_t *elab = nullptr;      // label of each entry's neighbour, CSR order (built on first use)
 };
 
 struct ccpm_tmpl {
@@ -2328,12 +2354,14 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
     std::lock_guard<std::mutex> lock(g->lrow_mu);
     if (g->lcol || g->m == 0) return CCPM_OK;
     int rc;
-    uint8_t *keys = nullptr;
+    uint8_t *keys = g->elab;        // the entry labels are the sort keys (gathered here if not built)
     if ((rc = dalloc(ctx, &g->lcol, (size_t)g->m))) return rc;
     if ((rc = dalloc(ctx, &g->nlab, (size_t)g->m))) return rc;
-    if ((rc = dalloc(ctx, &keys, (size_t)g->m))) return rc;
-    int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
-    k_gather_labels<<<grid, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, keys);
+    if (!keys) {
+        if ((rc = dalloc(ctx, &keys, (size_t)g->m))) return rc;
+        int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
+        k_gather_labels<<<grid, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, keys);
+    }
     size_t tmp_bytes = 0;
     cudaError_t e = cub::DeviceSegmentedSort::StableSortPairs(nullptr, tmp_bytes, keys, g->nlab, g->col, g->lcol,
                                                               g->m, g->n, g->rp, g->rp + 1, ctx->stream);
@@ -2344,7 +2372,7 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
                                                       g->m, g->n, g->rp, g->rp + 1, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(tmp);
-    cudaFree(keys);
+    if (keys != g->elab) cudaFree(keys);
     if (e != cudaSuccess) {
         cudaFree(g->lcol); cudaFree(g->nlab);
         g->lcol = nullptr; g->nlab = nullptr;
@@ -2352,6 +2380,28 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
                        std::string("label-grouped rows: ") + cudaGetErrorString(e));
     }
     g->lrows_ready.store(true);
+    return CCPM_OK;
+}
+
+// The label of every entry's neighbour in CSR order (one byte per entry):
+// the first LCC round after init reads it instead of the column index and the
+// neighbour's label.  Built once per graph, the first time a first round
+// covers a large share of the entries.
+int ensure_entry_labels(ccpm_ctx *ctx, ccpm_graph *g) {
+    std::lock_guard<std::mutex> lock(g->lrow_mu);
+    if (g->elab || g->m == 0) return CCPM_OK;
+    uint8_t *el = nullptr;
+    int rc;
+    if ((rc = dalloc(ctx, &el, (size_t)g->m))) return rc;
+    int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_gather_labels<<<grid, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, el);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(el);
+        return set_err(ctx, CCPM_ECUDA, std::string("entry labels: ") + cudaGetErrorString(e));
+    }
+    g->elab = el;
     return CCPM_OK;
 }
 
@@ -2497,6 +2547,8 @@ struct Pipeline {
     int short_max = kSmallDeg;      // rows up to this length take the flat short-row path
     bool eta_off = false;           // ablation: no edge elimination
     int nw_bytes = 0;               // width of the narrow copy of omega (0: none)
+    const uint8_t *elab = nullptr;  // the graph's entry labels for the first round (or none)
+    int64_t first_rows = 0;         // entries in the rows of the initially active vertices
     // rows the LCC rounds read: the graph's, or the latest compacted ones (K4)
     const int64_t *lrp = nullptr;
     const int32_t *lcol = nullptr;
@@ -2563,6 +2615,7 @@ struct Pipeline {
         a.hub_deg = w.hub_deg;
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
         a.lab0 = from_labels ? g->lab : nullptr;
+        a.elab = from_labels ? elab : nullptr;
         a.lmask = lm0;
         a.eta_off = eta_off ? ~0u : 0u;
         a.nw_bytes = nw_bytes;
@@ -2976,6 +3029,7 @@ void ccpm_graph_destroy(ccpm_graph_t g) {
     if (!g->borrowed) { cudaFree(g->rp); cudaFree(g->col); cudaFree(g->lab); }
     cudaFree(g->lcol);
     cudaFree(g->nlab);
+    cudaFree(g->elab);
     delete g;
 }
 
@@ -3165,8 +3219,16 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     P.n_small = w.st_h->n_small;
     P.n_med = w.st_h->n_med;
     P.n_chunk = w.st_h->n_chunk;
+    P.first_rows = (int64_t)w.st_h->row_entries;
     if (w.st_h->n_hub_slots > (unsigned)w.acc_cap || P.n_chunk > w.chunk_cap)
         return fail(set_err(ctx, CCPM_EOVERFLOW, "hub bookkeeping overflow"));
+    // the first round reads the entry labels when its rows cover a large
+    // share of the graph (building them is one pass over the entries)
+    if (P.dense && (opt.entry_labels > 0 ||
+                    (opt.entry_labels == 0 && P.first_rows >= kEntryLabelRows && P.first_rows * 8 >= g->m))) {
+        RCF(ensure_entry_labels(ctx, g));
+        P.elab = g->elab;
+    }
 
     // ---- LCC to fixpoint (Alg. 4)
     P.searches_ahead = opt.lcc_only ? 0 : (int)t.order.size();
@@ -3563,10 +3625,16 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         final_done = true;
     }
     if (!final_done) {
-        // hand back the pruned state: exact edge map for live rows, dead rows zeroed
+        // hand back the pruned state: exact edge map for live rows, dead rows
+        // zeroed.  When every round ran on the full rows with edge
+        // elimination, the last (quiescent) round has already left the live
+        // rows exact, and only the rows of dead vertices are cleared.
         P.launches++;
-        k_materialize_fix<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, g->col,
-                                                                           w.ebits, P.dt);
+        if (P.gen < 0 && !P.eta_off)
+            k_clear_dead_rows<<<grid_for(ctx, g->n, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, w.ebits);
+        else
+            k_materialize_fix<<<grid_for(ctx, g->n * 32, 256, 8), 256, 0, s>>>(g->n, w.om[P.cur], g->rp, g->col,
+                                                                               w.ebits, P.dt);
         CUF(cudaGetLastError());
         CUF(cudaMemcpyAsync(r->om, w.om[P.cur], sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
         CUF(cudaMemcpyAsync(r->eb, w.ebits, sizeof(uint32_t) * (size_t)w.words, cudaMemcpyDeviceToDevice, s));
@@ -4458,6 +4526,7 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         a.med_chunk = 1;
         a.small_chunk = 8;
         a.lab0 = nullptr;
+        a.elab = nullptr;
         a.prev = nullptr;
         a.resident_warps = num_sms * 32;
         a.eta_off = 0u;

@@ -259,3 +259,37 @@ def test_edge_elimination_ablation_keeps_the_result(ctx):
         np.testing.assert_array_equal(on["omega"], off["omega"])
         np.testing.assert_array_equal(on["ebits"], off["ebits"])
         assert on["counts"]["match_embeddings"] == off["counts"]["match_embeddings"]
+
+
+def test_entry_label_first_round(ctx):
+    # options.entry_labels: the first round reads the per-graph copy of the
+    # neighbour labels in entry order instead of the column index and the
+    # label gather; the whole pipeline stays oracle-exact, on the short-row,
+    # warp-per-row and split-row paths, with and without the final search
+    g = wl.rmat_graph(14, seed=12)
+    tl, te = [5, 4, 8, 7, 4, 5], [(0, 1), (1, 2), (1, 3), (3, 4), (3, 5), (2, 3)]
+    for opt in (dict(entry_labels=1), dict(entry_labels=1, hub_degree=8, short_rows=4)):
+        assert_parity(ctx, g, tl, te, **opt)
+    ref = pipeline.run(g.row_ptr, g.col, g.labels, tl, te)
+    from oracle import pack_bits
+    for el in (1, -1):
+        gpu = gpu_run(ctx, g, tl, te, entry_labels=el, run_final=0)
+        np.testing.assert_array_equal(gpu["omega"], ref.omega_pre_final)
+        np.testing.assert_array_equal(gpu["ebits"], pack_bits(ref.A_pre_final))
+    # the first LCC fixpoint alone (every round on the full rows): the live
+    # rows are exact after the quiescent round, the dead rows are zeroed
+    g.labels = np.zeros(g.n, dtype=np.uint8)
+    g.labels[::3] = 1
+    tl2, te2 = [0, 1, 0, 0], [(0, 1), (1, 2), (2, 3), (3, 0)]
+    import oracle
+    og = oracle.Graph(g.row_ptr, g.col, g.labels)
+    om_o, A_o = oracle.init(og, tl2, te2)
+    rounds, scanned = oracle.lcc(og, tl2, te2, om_o, A_o)
+    assert np.count_nonzero(om_o) > 0
+    for el in (1, -1):
+        for comp in (-1, 1):
+            gpu = gpu_run(ctx, g, tl2, te2, entry_labels=el, lcc_only=1, compact=comp)
+            assert gpu["phases"] == [rounds]
+            assert gpu["counts"]["edges_scanned_lcc"] == scanned
+            np.testing.assert_array_equal(gpu["omega"], om_o)
+            np.testing.assert_array_equal(gpu["ebits"], oracle.pack_bits(A_o))
