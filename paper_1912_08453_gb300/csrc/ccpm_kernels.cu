@@ -1243,6 +1243,7 @@ struct WarpSearch {
     // its last positions, and only what differs needs marking
     const DevPlan *last_plan;
     int32_t last[kMaxT];
+    unsigned long long pub;     // matches of this warp already added to the global count
 };
 constexpr int kJoinCache = 2, kJoinCacheLen = 128;
 
@@ -1580,10 +1581,20 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
                 // question already, or has the count run past its cap?
                 unsigned int stop = 0;
                 if (lane == 0) {
-                    if (MODE == kExist)
+                    if (MODE == kExist) {
                         stop = W.done_word && (*(volatile const uint32_t *)W.done_word & W.done_bit);
-                    else
+                    } else if (MODE == kCount || MODE == kMark) {
+                        // counting (and marking) stops as soon as the total passes
+                        // the cap: publish this warp's new matches and read the
+                        // total, so that no warp runs on to the cap by itself
+                        const unsigned long long d = matches - W.pub;
+                        const unsigned long long tot =
+                            d ? atomicAdd(&a.st->matches, d) + d : *(volatile const unsigned long long *)&a.st->matches;
+                        W.pub = matches;
+                        stop = tot > a.cap || *(volatile const unsigned int *)&a.st->overflow;
+                    } else {
                         stop = matches > a.cap || *(volatile const unsigned int *)&a.st->overflow;
+                    }
                 }
                 if (__shfl_sync(FULL_MASK, stop, 0)) {
                     if (MODE == kCount) over = true;
@@ -1666,7 +1677,7 @@ k_final_search(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
-    if (lane == 0) W.last_plan = nullptr;
+    if (lane == 0) { W.last_plan = nullptr; W.pub = 0; }
     __syncwarp();
     unsigned long long entries = 0, matches = 0;
     bool over = false;
@@ -1675,15 +1686,20 @@ k_final_search(SearchArgs a) {
         if (lane == 0) stop = *(volatile unsigned int *)&a.st->overflow;
         if (__shfl_sync(FULL_MASK, stop, 0)) break;
         const int32_t v = a.roots[it];
-        unsigned long long before = matches;
         if (lane == 0) { W.psi[0] = v; W.done_word = nullptr; }
         __syncwarp();
         search_from<MODE>(a, a.plans[0], 1, W, entries, matches, over);
         __syncwarp();
-        if (matches != before) {
+        const unsigned long long pub = W.pub;     // read by every lane before lane 0 moves it
+        __syncwarp();
+        if (matches != pub) {
             unsigned long long tot = 0;
-            if (lane == 0) tot = atomicAdd(&a.st->matches, matches - before) + (matches - before);
+            if (lane == 0) {
+                tot = atomicAdd(&a.st->matches, matches - pub) + (matches - pub);
+                W.pub = matches;
+            }
             tot = __shfl_sync(FULL_MASK, tot, 0);
+            __syncwarp();
             if (tot > a.cap) over = true;
         }
         if (over) {
@@ -1854,7 +1870,7 @@ k_final_items(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int lane = (int)lane_id();
     WarpSearch &W = ws[wib];
-    if (lane == 0) W.last_plan = nullptr;
+    if (lane == 0) { W.last_plan = nullptr; W.pub = 0; }
     __syncwarp();
     unsigned long long entries = 0, matches = 0;
     bool over = false;
@@ -1863,7 +1879,6 @@ k_final_items(SearchArgs a) {
         if (lane == 0) stop = *(volatile unsigned int *)&a.st->overflow;
         if (__shfl_sync(FULL_MASK, stop, 0)) break;
         const int64_t it1 = min(a.n_items, it0 + kItemBatch);
-        const unsigned long long before = matches;
         for (int64_t it = it0; it < it1 && !over; it++) {
             const SearchItem item = a.items[it];
             const int depth = item.hd >> 8;
@@ -1873,10 +1888,16 @@ k_final_items(SearchArgs a) {
             search_from<MODE>(a, a.plans[0], depth, W, entries, matches, over);
             __syncwarp();
         }
-        if (matches != before) {
+        const unsigned long long pub = W.pub;     // read by every lane before lane 0 moves it
+        __syncwarp();
+        if (matches != pub) {
             unsigned long long tot = 0;
-            if (lane == 0) tot = atomicAdd(&a.st->matches, matches - before) + (matches - before);
+            if (lane == 0) {
+                tot = atomicAdd(&a.st->matches, matches - pub) + (matches - pub);
+                W.pub = matches;
+            }
             tot = __shfl_sync(FULL_MASK, tot, 0);
+            __syncwarp();
             if (tot > a.cap) over = true;
         }
         if (over) {
