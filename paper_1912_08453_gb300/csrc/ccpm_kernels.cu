@@ -259,6 +259,9 @@ struct LccArgs {
     // entry, built once per graph), so the first round reads neither the
     // column index nor the neighbour's label: omega(u) = lmask[elab[e]]
     const uint8_t *elab;
+    // later rounds over the full rows: warp-per-row paths visit only the set
+    // bits (most entries of a live row are inactive by then)
+    int sparse;
     // rounds queued without a host round trip: the list sizes come from the
     // previous round's counters, and a round after the fixpoint does nothing
     const RoundStats *prev;       // nullable: sizes are the fields above
@@ -298,6 +301,106 @@ struct Partial {
     }
 };
 
+// Position of the r-th (0-based) set bit of x (x has more than r set bits):
+// halve the range, keeping the half that holds it.
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t w = 16; w > 0; w >>= 1) {
+        const uint32_t low = __popc(x & ((1u << w) - 1u));
+        if (low <= r) { r -= low; x >>= w; pos += w; }
+    }
+    return pos;
+}
+
+template <int MAXC>
+__device__ __forceinline__ void tally_entry(uint32_t w, uint32_t nbr_v, const SmemTmpl &s, const uint32_t (&cm)[4],
+                                            Partial<MAXC> &p, uint32_t &scanned, bool &keep) {
+    keep = (w & nbr_v) != 0u;
+    scanned += w != 0u;
+    if (w != 0u && !keep) p.achg = 1u;  // eta eliminates the entry
+    if (keep) {
+        p.U |= w;
+        p.nN++;
+        if constexpr (MAXC > 0 && MAXC <= 4) {
+#pragma unroll
+            for (int c = 0; c < MAXC; c++) p.cnt[c] += (w & cm[c]) ? 1u : 0u;
+        } else {
+#pragma unroll
+            for (int c = 0; c < MAXC; c++)
+                if (c < s.n_cls) p.cnt[c] += (w & s.cls_mask[c]) ? 1u : 0u;
+        }
+    }
+}
+
+// Later rounds over the full rows, where most entries of a live row are
+// already inactive: only the entries whose bit is set are visited, 32 per
+// step (one per lane).  The bits of up to 1024 entries are read per load (one
+// word per lane); lane k takes the k-th set bit of the group by a search over
+// the words' prefix counts.  The next step's entries are located and their
+// column indices loaded while the current step's neighbour omegas are
+// gathered.  A failing entry's bit is cleared with an atomic (the words at
+// the ends of the range are shared with other rows).
+template <int MAXC>
+__device__ __forceinline__ void scan_row_sparse(int64_t beg, int64_t end, uint32_t nbr_v,
+                                                const int32_t *__restrict__ col, const uint32_t *__restrict__ om,
+                                                uint32_t *ebits, const SmemTmpl &s, Partial<MAXC> &p,
+                                                uint32_t &scanned, const uint32_t (&cm)[4], const void *nw, int nwb) {
+    const int lane = (int)lane_id();
+    const int64_t wb = beg >> 5, we = (end + 31) >> 5;
+    for (int64_t g0 = wb; g0 < we; g0 += 32) {
+        const int64_t wi = g0 + lane;
+        uint32_t word = 0u;
+        if (wi < we) {
+            word = ebits[wi];
+            const int64_t e0 = wi << 5;
+            if (e0 < beg) word &= ~0u << (uint32_t)(beg - e0);
+            if (end - e0 < 32) word &= (1u << (uint32_t)(end - e0)) - 1u;
+        }
+        const uint32_t c = __popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        const uint32_t excl = incl - c;
+        // lane k of a step: the (k0 + k)-th set entry of the group, and its column
+        auto locate = [&](uint32_t k0, int64_t &e, int32_t &u) {
+            const uint32_t k = k0 + (uint32_t)lane;
+            int i = 0;                                  // last word whose prefix is <= k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t ex = __shfl_sync(FULL_MASK, excl, i + step);
+                if (ex <= k) i += step;
+            }
+            const uint32_t wd = __shfl_sync(FULL_MASK, word, i);
+            const uint32_t ex_i = __shfl_sync(FULL_MASK, excl, i);
+            e = -1;
+            u = 0;
+            if (k < total) {
+                e = ((g0 + i) << 5) + (int64_t)select_bit(wd, k - ex_i);
+                u = __ldcs(col + e);
+            }
+        };
+        int64_t e_c = -1;
+        int32_t u_c = 0;
+        if (total) locate(0, e_c, u_c);
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t w = e_c >= 0 ? gather_om(om, nw, nwb, u_c) : 0u;
+            int64_t e_n = -1;
+            int32_t u_n = 0;
+            if (k0 + 32 < total) locate(k0 + 32, e_n, u_n);
+            bool keep;
+            tally_entry<MAXC>(w, nbr_v, s, cm, p, scanned, keep);
+            if (e_c >= 0 && !keep) atomicAnd(&ebits[e_c >> 5], ~(1u << (uint32_t)(e_c & 31)));
+            e_c = e_n;
+            u_c = u_n;
+        }
+    }
+}
+
 // Stream the CSR entries [beg, end) of an active vertex: edge elimination by
 // eta (entry kept iff the neighbour's omega contains a template neighbour of
 // some q in omega(v)), the union omega' of Alg. 4 and the per-class counts of
@@ -319,7 +422,13 @@ __device__ __forceinline__ void scan_row_warp(int64_t beg, int64_t end, uint32_t
                                               const SmemTmpl &s, Partial<MAXC> &p,
                                               uint32_t &scanned, const uint8_t *__restrict__ lab0,
                                               const uint32_t *slm, const uint32_t (&cm)[4], const void *nw,
-                                              int nwb, const uint8_t *__restrict__ elab) {
+                                              int nwb, const uint8_t *__restrict__ elab, bool sparse) {
+    if constexpr (!DENSE) {
+        if (sparse) {
+            scan_row_sparse<MAXC>(beg, end, nbr_v, col, om, ebits, s, p, scanned, cm, nw, nwb);
+            return;
+        }
+    }
     constexpr int UNR = 4;   // windows per step
     const int lane = (int)lane_id();
     const int64_t w0 = beg >> 5;
@@ -683,7 +792,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
         if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive += ci.c == 0; }
         Partial<MAXC> p;
         scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned, a.lab0,
-                                   slm, cm, a.nw_cur, a.nw_bytes, a.elab);
+                                   slm, cm, a.nw_cur, a.nw_bytes, a.elab, a.sparse != 0);
         p.U = grp_or<32>(p.U);
         p.nN = grp_sum<32>(p.nN);
         p.achg = grp_or<32>(p.achg);
@@ -751,7 +860,7 @@ k_lcc_round(LccArgs a, DevTmpl t) {
                 if (lane == 0) { tl.rows += (unsigned long long)(end - beg); tl.alive++; }
                 Partial<MAXC> p;
                 scan_row_warp<MAXC, DENSE>(beg, end, nbr_mask(wv, s) | a.eta_off, a.col, a.om_cur, a.ebits, s, p, tl.scanned,
-                                           a.lab0, slm, cm, a.nw_cur, a.nw_bytes, a.elab);
+                                           a.lab0, slm, cm, a.nw_cur, a.nw_bytes, a.elab, a.sparse != 0);
                 p.U = grp_or<32>(p.U);
                 p.nN = grp_sum<32>(p.nN);
                 p.achg = grp_or<32>(p.achg);
@@ -841,18 +950,6 @@ struct CompactArgs {
     int64_t *gdir;                // per slot: start of each label group, then the row end
     unsigned int *n_slots;        // slot counter (zeroed before)
 };
-
-// Position of the r-th (0-based) set bit of x (x has more than r set bits):
-// halve the range, keeping the half that holds it.
-__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r) {
-    uint32_t pos = 0;
-#pragma unroll
-    for (uint32_t w = 16; w > 0; w >>= 1) {
-        const uint32_t low = __popc(x & ((1u << w) - 1u));
-        if (low <= r) { r -= low; x >>= w; pos += w; }
-    }
-    return pos;
-}
 
 // Visit the entries of [beg, end) whose bit is set, 32 at a time and in
 // ascending order: f(e, valid) is called by all lanes, lane i with the i-th
@@ -1597,7 +1694,9 @@ __device__ bool search_from(const SearchArgs &a, const DevPlan &P, int d0, WarpS
                     }
                 }
                 if (__shfl_sync(FULL_MASK, stop, 0)) {
-                    if (MODE == kCount) over = true;
+                    // past the cap (the matches are published already, so the
+                    // caller's batch-end check would not see it)
+                    if (MODE == kCount || MODE == kMark) over = true;
                     return false;
                 }
             }
@@ -2637,6 +2736,7 @@ struct Pipeline {
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
         a.lab0 = from_labels ? g->lab : nullptr;
         a.elab = from_labels ? elab : nullptr;
+        a.sparse = (!dense && gen < 0) ? 1 : 0;
         a.lmask = lm0;
         a.eta_off = eta_off ? ~0u : 0u;
         a.nw_bytes = nw_bytes;
@@ -3937,7 +4037,6 @@ int ccpm_explore(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t base, int max_remov
     }
     auto cleanup = [&]() { cudaFree(c_om); cudaFree(c_eb); };
     auto fail_c = [&](int code) { cleanup(); return code; };
-    cudaEvent_t e0 = ctx->ws.ev[0], e1 = ctx->ws.ev[1];
     if (cudaMemsetAsync(c_om, 0, sizeof(uint32_t) * (size_t)g->n, s) != cudaSuccess ||
         cudaMemsetAsync(c_eb, 0, sizeof(uint32_t) * (size_t)(words + 1), s) != cudaSuccess)
         return fail_c(set_err(ctx, CCPM_ECUDA, "explore: memset"));
@@ -4019,7 +4118,6 @@ int ccpm_explore(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t base, int max_remov
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail_c(set_err(ctx, CCPM_ECUDA, "explore: sync"));
     cleanup();
-    (void)e0; (void)e1;
     if (n_variants) *n_variants = nv;
     if (level_found) *level_found = found;
     *out = u;
@@ -4548,6 +4646,7 @@ int lcc_fixpoint_noalloc_body(int device, void *cuda_stream, int64_t n, int64_t 
         a.small_chunk = 8;
         a.lab0 = nullptr;
         a.elab = nullptr;
+        a.sparse = 0;
         a.prev = nullptr;
         a.resident_warps = num_sms * 32;
         a.eta_off = 0u;
