@@ -75,6 +75,12 @@ def lib():
         L.oracle_final.restype = ctypes.c_int
         L.oracle_matches.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, ctypes.c_uint64, vp, vp]
         L.oracle_matches.restype = ctypes.c_uint64
+        L.oracle_wide_init.argtypes = [i64, vp, vp, vp, i32, vp, vp, vp]
+        L.oracle_wide_init.restype = None
+        L.oracle_wide_lcc_round.argtypes = [i64, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_wide_lcc_round.restype = ctypes.c_int
+        L.oracle_wide_lcc.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp]
+        L.oracle_wide_lcc.restype = ctypes.c_int64
         _libs[key] = L
     return _libs[key]
 
@@ -191,3 +197,66 @@ def pack_bits(A: np.ndarray) -> np.ndarray:
     out = np.zeros(words * 4, dtype=np.uint8)
     out[: b.shape[0]] = b
     return out.view("<u4").astype(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# Wider templates (n0 <= 64, 64-bit omega) and edge labels: the LCC phase.
+
+
+def _wide_template(labels, edges, edge_labels):
+    n0 = len(labels)
+    assert 2 <= n0 <= 64
+    tlab = np.zeros(64, dtype=np.uint8)
+    tlab[:n0] = labels
+    te = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    if te.size == 0:
+        te = np.zeros(2, dtype=np.int32)
+    tel = None
+    if edge_labels is not None:
+        tel = np.ascontiguousarray(np.asarray(edge_labels, dtype=np.uint8))
+        assert tel.shape[0] == len(edges)
+    return n0, tlab, te, tel
+
+
+def _opt(a):
+    return None if a is None else _p(a)
+
+
+def wide_init(g: Graph, labels):
+    n0 = len(labels)
+    tlab = np.zeros(64, dtype=np.uint8)
+    tlab[:n0] = labels
+    omega = np.ascontiguousarray(np.zeros(max(g.n, 1), dtype=np.uint64)[: g.n])
+    A = np.ascontiguousarray(np.zeros(max(g.m, 1), dtype=np.uint8)[: g.m])
+    lib().oracle_wide_init(g.n, _p(g.rp), _p(g.col), _p(g.lab), n0, _p(tlab), _p(omega), _p(A))
+    return omega, A
+
+
+def wide_lcc_round(g: Graph, labels, edges, omega, A, edge_labels=None, graph_edge_labels=None):
+    """One snapshot round with 64-bit omega and edge labels.
+    Returns (changed, omega', A', scanned)."""
+    n0, tlab, te, tel = _wide_template(labels, edges, edge_labels)
+    el = None if graph_edge_labels is None else np.ascontiguousarray(graph_edge_labels, dtype=np.uint8)
+    om2 = np.zeros_like(omega)
+    A2 = np.zeros_like(A)
+    sc = np.zeros(1, dtype=np.int64)
+    ch = lib().oracle_wide_lcc_round(g.n, _p(g.rp), _p(g.col), _opt(el), n0, _p(tlab), len(edges), _p(te),
+                                     _opt(tel), _p(omega), _p(A), _p(om2), _p(A2), _p(sc))
+    if ch < 0:
+        raise MemoryError("oracle_wide_lcc_round")
+    return bool(ch), om2, A2, int(sc[0])
+
+
+def wide_lcc(g: Graph, labels, edges, edge_labels=None, graph_edge_labels=None):
+    """Init and LCC to its fixpoint with 64-bit omega and edge labels.
+    Returns (omega uint64[n], A uint8[m], rounds, scanned)."""
+    n0, tlab, te, tel = _wide_template(labels, edges, edge_labels)
+    el = None if graph_edge_labels is None else np.ascontiguousarray(graph_edge_labels, dtype=np.uint8)
+    omega = np.ascontiguousarray(np.zeros(max(g.n, 1), dtype=np.uint64)[: g.n])
+    A = np.ascontiguousarray(np.zeros(max(g.m, 1), dtype=np.uint8)[: g.m])
+    sc = np.zeros(1, dtype=np.int64)
+    r = lib().oracle_wide_lcc(g.n, _p(g.rp), _p(g.col), _p(g.lab), _opt(el), n0, _p(tlab), len(edges), _p(te),
+                              _opt(tel), _p(omega), _p(A), _p(sc))
+    if r < 0:
+        raise MemoryError("oracle_wide_lcc")
+    return omega, A, int(r), int(sc[0])

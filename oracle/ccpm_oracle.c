@@ -497,3 +497,185 @@ uint64_t oracle_matches(int64_t n, const int64_t *rp, const int32_t *col,
     }
     return s.count;
 }
+
+/* ======================================================================== */
+/* Wider templates and edge labels (the LCC phase only).                     */
+/*                                                                          */
+/* The paper's LCC storage estimate budgets eight bytes of omega per vertex  */
+/* for a template of 64 vertices (Section 5.1), and its graphs carry         */
+/* metadata on edges as well as vertices (Section 3).  Here omega is a       */
+/* 64-bit word (bit q = template vertex q, n0 <= 64), graph entry e carries  */
+/* the edge label el[e] (the same on both directions of an edge; all 0 when  */
+/* el is NULL) and template edge i carries tel[i] (all 0 when tel is NULL).  */
+/* A match must map every template edge onto a graph edge of the same label, */
+/* so the local constraints of Alg. 4 read, per edge label L:                */
+/*  - eta: entry (v,u) labelled L survives iff some a in omega(v) has a      */
+/*    template neighbour b in omega(u) joined to a by an edge labelled L;    */
+/*  - coverage: each template neighbour b of q, joined by label L, lies in   */
+/*    omega(u) for some surviving entry (v,u) labelled L;                    */
+/*  - multiplicity: for each pair (vertex label, edge label), at least as    */
+/*    many distinct surviving neighbours u reached by that edge label have   */
+/*    omega(u) meeting q's template neighbours of that pair as q has such    */
+/*    neighbours.                                                            */
+/* With every edge label 0 these are exactly the rules of oracle_lcc_round.  */
+/* Rounds are snapshot (Jacobi) rounds, counted as in oracle_lcc.            */
+/* ======================================================================== */
+
+typedef struct {
+    int n0;
+    uint8_t tlab[64];
+    uint64_t adj[256][64];   /* adj[L][q]: template neighbours of q via edges labelled L */
+    uint64_t any[64];        /* template neighbours of q, any edge label */
+} wide_tmpl_t;
+
+static int popc64(uint64_t x) { int c = 0; while (x) { x &= x - 1; c++; } return c; }
+
+static void wide_tables(int n0, const uint8_t *tlab, int m0, const int32_t *te, const uint8_t *tel,
+                        wide_tmpl_t *t)
+{
+    memset(t, 0, sizeof(*t));
+    t->n0 = n0;
+    for (int q = 0; q < n0; q++) t->tlab[q] = tlab[q];
+    for (int i = 0; i < m0; i++) {
+        int a = te[2 * i], b = te[2 * i + 1];
+        int L = tel ? tel[i] : 0;
+        t->adj[L][a] |= 1ull << b;
+        t->adj[L][b] |= 1ull << a;
+        t->any[a] |= 1ull << b;
+        t->any[b] |= 1ull << a;
+    }
+}
+
+/* eta with an edge label: some a in wv has a template neighbour in wu via label L */
+static int wide_compatible(const wide_tmpl_t *t, uint64_t wv, uint64_t wu, int L)
+{
+    for (int a = 0; a < t->n0; a++)
+        if ((wv >> a) & 1ull)
+            if (t->adj[L][a] & wu) return 1;
+    return 0;
+}
+
+/* Alg. 3 with 64-bit omega: omega(v) = {q : l(q) = l(v)}; an entry is active
+ * iff both of its ends are. */
+void oracle_wide_init(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *lab,
+                      int n0, const uint8_t *tlab, uint64_t *omega, uint8_t *A)
+{
+    for (int64_t v = 0; v < n; v++) {
+        uint64_t w = 0;
+        for (int q = 0; q < n0; q++)
+            if (tlab[q] == lab[v]) w |= 1ull << q;
+        omega[v] = w;
+    }
+    for (int64_t v = 0; v < n; v++)
+        for (int64_t e = rp[v]; e < rp[v + 1]; e++)
+            A[e] = (omega[v] != 0 && omega[col[e]] != 0) ? 1 : 0;
+}
+
+static int wide_round(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *el,
+                      const wide_tmpl_t *t, const uint64_t *om_in, const uint8_t *A_in,
+                      uint64_t *om_out, uint8_t *A_out, int64_t *scanned)
+{
+    int changed = 0;
+    int64_t sc = 0;
+    static uint64_t U[256];   /* omega' per edge label (single-threaded use) */
+    for (int64_t v = 0; v < n; v++) {
+        uint64_t wv = om_in[v];
+        if (wv == 0) { om_out[v] = 0; continue; }
+        memset(U, 0, sizeof(U));
+        int64_t n_alive_edges = 0;
+        for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
+            if (!A_in[e]) continue;
+            sc += 1;
+            int L = el ? el[e] : 0;
+            uint64_t wu = om_in[col[e]];
+            if (!wide_compatible(t, wv, wu, L)) continue;
+            U[L] |= wu;
+            n_alive_edges++;
+        }
+        uint64_t keep = 0;
+        for (int q = 0; q < t->n0; q++) {
+            if (!((wv >> q) & 1ull)) continue;
+            int ok = 1;
+            /* coverage, edge label by edge label */
+            for (int L = 0; ok && L < 256; L++)
+                if (t->adj[L][q] & ~U[L]) ok = 0;
+            /* distinct-neighbour multiplicity per (vertex label, edge label) */
+            for (int L = 0; ok && L < 256; L++) {
+                for (int b = 0; ok && b < t->n0; b++) {
+                    if (!((t->adj[L][q] >> b) & 1ull)) continue;
+                    uint64_t cls = 0;
+                    for (int c = 0; c < t->n0; c++)
+                        if (((t->adj[L][q] >> c) & 1ull) && t->tlab[c] == t->tlab[b]) cls |= 1ull << c;
+                    int need = popc64(cls);
+                    int have = 0;
+                    for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
+                        if (!A_in[e]) continue;
+                        if ((el ? el[e] : 0) != L) continue;
+                        uint64_t wu = om_in[col[e]];
+                        if (!wide_compatible(t, wv, wu, L)) continue;
+                        if (wu & cls) have++;
+                    }
+                    if (have < need) ok = 0;
+                }
+            }
+            if (ok) keep |= 1ull << q;
+        }
+        if (n_alive_edges == 0) keep = 0;
+        om_out[v] = keep;
+        if (keep != wv) changed = 1;
+    }
+    *scanned += sc;
+    for (int64_t v = 0; v < n; v++) {
+        for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
+            int64_t u = col[e];
+            uint8_t a = A_in[e];
+            if (a && !wide_compatible(t, om_in[v], om_in[u], el ? el[e] : 0)) a = 0;
+            if (om_out[v] == 0 || om_out[u] == 0) a = 0;
+            A_out[e] = a;
+            if (a != A_in[e]) changed = 1;
+        }
+    }
+    return changed;
+}
+
+/* One snapshot round (for the tests of single rounds).  Returns 1 if omega or
+ * A changed. */
+int oracle_wide_lcc_round(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *el,
+                          int n0, const uint8_t *tlab, int m0, const int32_t *te, const uint8_t *tel,
+                          const uint64_t *om_in, const uint8_t *A_in, uint64_t *om_out, uint8_t *A_out,
+                          int64_t *scanned)
+{
+    wide_tmpl_t *t = (wide_tmpl_t *)malloc(sizeof(wide_tmpl_t));
+    if (!t) return -1;
+    wide_tables(n0, tlab, m0, te, tel, t);
+    int ch = wide_round(n, rp, col, el, t, om_in, A_in, om_out, A_out, scanned);
+    free(t);
+    return ch;
+}
+
+/* Init, then rounds until one changes nothing.  Returns the rounds executed
+ * (the quiescent one included), or -1 on allocation failure. */
+int64_t oracle_wide_lcc(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *lab, const uint8_t *el,
+                        int n0, const uint8_t *tlab, int m0, const int32_t *te, const uint8_t *tel,
+                        uint64_t *omega, uint8_t *A, int64_t *scanned)
+{
+    int64_t m = rp[n];
+    wide_tmpl_t *t = (wide_tmpl_t *)malloc(sizeof(wide_tmpl_t));
+    uint64_t *om2 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t *A2 = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+    if (!t || !om2 || !A2) { free(t); free(om2); free(A2); return -1; }
+    wide_tables(n0, tlab, m0, te, tel, t);
+    oracle_wide_init(n, rp, col, lab, n0, tlab, omega, A);
+    int64_t rounds = 0;
+    int changed;
+    do {
+        changed = wide_round(n, rp, col, el, t, omega, A, om2, A2, scanned);
+        memcpy(omega, om2, sizeof(uint64_t) * (size_t)n);
+        memcpy(A, A2, (size_t)m);
+        rounds++;
+    } while (changed);
+    free(t);
+    free(om2);
+    free(A2);
+    return rounds;
+}

@@ -176,6 +176,37 @@ def graph_from_edge_list(n: int, edges, labels) -> Graph:
     return Graph(n, row_ptr, col, np.asarray(labels, dtype=np.uint8))
 
 
+def edge_labels(row_ptr: np.ndarray, col: np.ndarray, n_labels: int, seed: int = 3,
+                weights=None) -> np.ndarray:
+    """One label per undirected edge, the same on both of its CSR entries:
+    edge {x, y} (x < y) draws from a Philox stream keyed by the edge, so the
+    two directions agree without a lookup.  `weights` (optional) skews the
+    distribution over 0..n_labels-1.  Returns uint8 [m_dir] in entry order."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    c = np.asarray(col, dtype=np.int64)
+    n = rp.shape[0] - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    lo, hi = np.minimum(src, c), np.maximum(src, c)
+    key = (lo.astype(np.uint64) << np.uint64(32)) | hi.astype(np.uint64)
+    u = _edge_uniform(key, seed)
+    if weights is None:
+        return (np.floor(u * n_labels).astype(np.int64) % n_labels).astype(np.uint8)
+    w = np.asarray(weights, dtype=np.float64)
+    cdf = np.cumsum(w / w.sum())
+    return np.minimum(np.searchsorted(cdf, u, side="right"), n_labels - 1).astype(np.uint8)
+
+
+def _edge_uniform(key: np.ndarray, seed: int) -> np.ndarray:
+    """Uniform [0, 1) per 64-bit key: Philox4x32-10 with the key as counter."""
+    import torch
+    k = torch.from_numpy(key.view(np.int64))
+    c0 = k & _U32
+    c1 = (k >> 32) & _U32
+    z = torch.zeros_like(c0)
+    r0, _, _, _ = philox4x32(c0, c1, z, z, seed & _U32, 0x2545F491)
+    return r0.numpy().astype(np.float64) / 4294967296.0
+
+
 def label_frequencies(g: Graph, n_labels: int = 256) -> np.ndarray:
     return np.bincount(g.labels, minlength=n_labels)[:n_labels].astype(np.int64)
 
