@@ -126,6 +126,11 @@ typedef struct {
                                    /* entry, built once): 0 = when the initially   */
                                    /* active rows hold >= 1/8 of the entries and   */
                                    /* >= 2^22, 1 = always, -1 = never; same result */
+    int      grid_share;           /* ccpm_prune_batch: each worker sizes its grids */
+                                   /* for 1/grid_share of the GPU's SMs, so that  */
+                                   /* kernels of several templates run side by   */
+                                   /* side instead of one filling every SM:       */
+                                   /* 0 = the autotuned choice, 1 = the whole GPU */
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 
@@ -252,13 +257,15 @@ int  ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t t,
  * concurrently on worker streams of this context, each with its own scratch,
  * so that small phases of different templates overlap on the GPU.  With
  * options.batch_workers = 0 the settings come from an autotuner: on the first
- * call for this graph it prunes one slice of the batch (its first 8
- * templates) once per candidate setting and keeps the fastest, choosing in
- * turn the worker count (4, 8, 16), options.search_split (2048, 512, 8192),
- * options.short_rows (64, 32, 256) and options.hub_degree (1024, 4096); the
- * choice is kept on the graph and applies to options left at 0.  Every
- * setting gives the same results.  outs[i] follows the same create-or-reuse
- * rule as ccpm_prune.  Returns CCPM_OK, CCPM_EBUDGET if any template hit a budget
+ * call for this graph it prunes one slice of the batch (32 templates spread
+ * evenly over it) once per candidate setting and keeps the fastest, choosing
+ * in turn the worker count (1, 2, 4, 8, 16), options.grid_share (1, 2, 4),
+ * options.search_split (2048, 512, 8192), options.short_rows (64, 32, 256)
+ * and options.hub_degree (1024, 4096); the choice is kept on the graph and
+ * applies to options left at 0.  When every outs[i] holds a result of an
+ * earlier call, the templates start longest first by that result's time.
+ * Every setting gives the same results.  outs[i] follows the same
+ * create-or-reuse rule as ccpm_prune.  Returns CCPM_OK, CCPM_EBUDGET if any template hit a budget
  * (see each result's counts), or the first error. */
 int  ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *tmpls,
                       const ccpm_options *opt, ccpm_result_t *outs);
@@ -267,9 +274,10 @@ int  ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *
 int  ccpm_graph_batch_workers(ccpm_graph_t g);
 /* All the autotuner's choices for g (zeros before the first autotuned batch;
  * 0 for search_split, short_rows or hub_degree = the library default) and
- * the chosen setting's wall time on the tuning slice in milliseconds. */
-int  ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *search_split, int *short_rows, int *hub_degree,
-                             double *slice_ms);
+ * the chosen setting's wall time on the tuning slice in milliseconds.  Any
+ * pointer may be NULL. */
+int  ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *grid_share, int *search_split, int *short_rows,
+                             int *hub_degree, double *slice_ms);
 
 /* ----------------------------------------------------------------- result */
 
@@ -399,6 +407,56 @@ int  ccpm_mlp_gradient(ccpm_mlp_t m, int B, const float *x, const float *t, floa
  * *final_loss (nullable) gets the last minibatch's loss. */
 int  ccpm_mlp_train(ccpm_mlp_t m, int N, const float *x, const float *t, int steps, int batch, float lr,
                     uint64_t seed, float *final_loss);
+
+/* ------------------------------------ wider templates and edge labels */
+
+/* Edge labels of a loaded graph (Section 3: the background graph carries
+ * metadata on its edges as well as on its vertices).  edge_labels[e] is the
+ * label of CSR entry e, uint8 [m_dir]; both entries of an undirected edge
+ * must carry the same label (checked with CCPM_VALIDATE, host pointers only:
+ * CCPM_EINVAL otherwise).  CCPM_HOST_PTRS copies the array to the device;
+ * CCPM_DEVICE_PTRS borrows it (it must outlive the graph).  A later call
+ * replaces the labels; NULL removes them (every edge label is then 0).  Only
+ * ccpm_lcc_wide reads them. */
+int  ccpm_graph_set_edge_labels(ccpm_graph_t g, const uint8_t *edge_labels, int flags);
+
+typedef struct {
+    int64_t rounds;          /* LCC rounds executed, the final quiescent one included */
+    int64_t edges_scanned;   /* active entries read, summed over the rounds           */
+    int64_t active_v;        /* vertices whose omega is not empty at the fixpoint     */
+    int64_t active_e_dir;    /* CSR entries whose bit is set at the fixpoint          */
+    double  ms;              /* device time of the call (events on the ctx stream)    */
+} ccpm_wide_stats;
+
+/* Local constraint checking to its fixpoint for templates of up to 64
+ * vertices, with edge labels.  The paper sizes LCC state at eight bytes of
+ * omega per vertex for a 64-vertex template (Section 5.1, "Complexity
+ * Analysis"), and a match must preserve edge metadata as well as vertex
+ * labels (Section 3).
+ *   template: n0 (2..64) vertex labels, m0 (1..2016) edges as 2*m0 int32
+ *             (endpoints in range, no self loop or duplicate, connected), and
+ *             tmpl_edge_labels (nullable: all 0), one label per edge; at most
+ *             8 distinct edge labels and 64 label-multiplicity classes
+ *   graph:    its edge labels from ccpm_graph_set_edge_labels (all 0 if none)
+ * Per edge label L, the rules of Alg. 4 read: an active entry (v,u) labelled L
+ * stays active iff some a in omega(v) has a template neighbour b in omega(u)
+ * joined to a by an edge labelled L; q stays in omega(v) iff every template
+ * neighbour b of q (joined by label L) lies in omega(u) for some entry (v,u)
+ * labelled L that stays active, and, for every pair (vertex label, edge
+ * label), at least as many distinct such neighbours u reached by that edge
+ * label have omega(u) meeting q's template neighbours of that pair as q has
+ * such neighbours.  Rounds are snapshot rounds.  With every edge label 0 and
+ * n0 <= 32 the result equals the first LCC fixpoint of ccpm_prune.
+ * Outputs: omega uint64 [n] (bit q = template vertex q) and the edge bitmap
+ * (ceil(m_dir/32) uint32 words, layout as above), device pointers on the
+ * context's device if out_on_device, else host memory; stats (nullable).  No
+ * non-local constraint and no final search run: the result holds every match
+ * (a superset of omega* and E*; exact for acyclic templates with unique
+ * vertex labels).  Synchronous on the context's stream.  Errors: CCPM_EINVAL
+ * (template, with a message in ccpm_last_error), CCPM_ENOMEM, CCPM_ECUDA. */
+int  ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8_t *tmpl_labels, int m0,
+                   const int32_t *tmpl_edges, const uint8_t *tmpl_edge_labels, uint64_t *omega,
+                   uint32_t *ebits, int out_on_device, ccpm_wide_stats *stats);
 
 /* ------------------------------------------------- allocation-free LCC */
 

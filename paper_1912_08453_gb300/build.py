@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccpm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ccpm_kernels.cu", "ccpm_mlp.cu", "ccpm_host.cpp"]
+SOURCES = ["ccpm_kernels.cu", "ccpm_mlp.cu", "ccpm_wide.cu", "ccpm_host.cpp"]
 
 
 def _nvcc():

@@ -39,8 +39,13 @@ class Options(ctypes.Structure):
                 ("hub_degree", ctypes.c_int), ("batch_workers", ctypes.c_int), ("resume", ctypes.c_int),
                 ("compact", ctypes.c_int), ("search_split", ctypes.c_int),
                 ("lcc_only", ctypes.c_int), ("short_rows", ctypes.c_int), ("no_edge_elimination", ctypes.c_int),
-                ("entry_labels", ctypes.c_int),
+                ("entry_labels", ctypes.c_int), ("grid_share", ctypes.c_int),
                 ("mlp", ctypes.c_void_p)]
+
+
+class WideStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("edges_scanned", ctypes.c_int64), ("active_v", ctypes.c_int64),
+                ("active_e_dir", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
 class Counts(ctypes.Structure):
@@ -129,13 +134,15 @@ def _load():
         "ccpm_mlp_gradient": ([vp, i32, vp, vp, vp, P(ctypes.c_float)], i32),
         "ccpm_mlp_train": ([vp, i32, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)], i32),
         "ccpm_graph_batch_workers": ([vp], i32),
-        "ccpm_graph_batch_tuning": ([vp, P(i32), P(i32), P(i32), P(i32), P(ctypes.c_double)], i32),
+        "ccpm_graph_batch_tuning": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(ctypes.c_double)], i32),
         "ccpm_result_matches": ([vp, vp, vp, P(Options), vp, ctypes.c_uint64, vp, vp, i32,
                                  P(ctypes.c_uint64)], i32),
         "ccpm_explore": ([vp, vp, vp, i32, P(Options), P(ExploreVariant), i32, P(i32), P(i32),
                           P(ctypes.c_double), P(vp)], i32),
         "ccpm_state_export": ([vp, vp, P(ctypes.c_size_t)], i32),
         "ccpm_state_import": ([vp, vp, vp, vp, ctypes.c_size_t, P(vp)], i32),
+        "ccpm_graph_set_edge_labels": ([vp, vp, i32], i32),
+        "ccpm_lcc_wide": ([vp, vp, i32, vp, i32, vp, vp, vp, vp, i32, P(WideStats)], i32),
         "ccpm_lcc_fixpoint_noalloc": ([i32, vp, i64, i64, vp, vp, vp, i32, vp, i32, vp, vp, vp,
                                        P(ctypes.c_int32), P(ctypes.c_int64), ctypes.c_char_p, ctypes.c_size_t], i32),
     }
@@ -158,7 +165,7 @@ EXPORTED = ["ccpm_ctx_create", "ccpm_ctx_destroy", "ccpm_last_error", "ccpm_opti
             "ccpm_result_constraint_log", "ccpm_mlp_create", "ccpm_mlp_destroy", "ccpm_mlp_set_params",
             "ccpm_mlp_get_params", "ccpm_mlp_forward", "ccpm_mlp_gradient", "ccpm_mlp_train",
             "ccpm_state_export", "ccpm_state_import", "ccpm_graph_batch_workers", "ccpm_result_matches", "ccpm_explore",
-            "ccpm_graph_batch_tuning"]
+            "ccpm_graph_batch_tuning", "ccpm_graph_set_edge_labels", "ccpm_lcc_wide"]
 
 
 def _ptr(a):
@@ -228,6 +235,20 @@ class Graph:
         self.words = (m + 31) // 32
         self._keep = (row_ptr, col, labels) if d0 else None
 
+    def set_edge_labels(self, edge_labels, validate: bool = False):
+        """Edge label of every CSR entry (uint8 [m_dir], the same on both
+        entries of an edge; ccpm_graph_set_edge_labels).  None removes them."""
+        if edge_labels is None:
+            self.ctx.check(lib.ccpm_graph_set_edge_labels(self.h, None, CCPM_HOST_PTRS), "ccpm_graph_set_edge_labels")
+            self._el = None
+            return
+        if int(edge_labels.shape[0]) != self.m:
+            raise ValueError(f"edge labels hold {int(edge_labels.shape[0])} entries, the graph {self.m}")
+        p, dev = _ptr(edge_labels)
+        flags = (CCPM_DEVICE_PTRS if dev else CCPM_HOST_PTRS) | (CCPM_VALIDATE if validate else 0)
+        self.ctx.check(lib.ccpm_graph_set_edge_labels(self.h, p, flags), "ccpm_graph_set_edge_labels")
+        self._el = edge_labels if dev else None     # borrowed device arrays must stay alive
+
     def close(self):
         if self.h:
             lib.ccpm_graph_destroy(self.h)
@@ -240,13 +261,34 @@ class Graph:
             pass
 
 
+def lcc_wide(ctx, graph, labels, edges, edge_labels=None):
+    """LCC fixpoint for templates of up to 64 vertices with edge labels
+    (ccpm_lcc_wide).  Returns (omega uint64 [n], edge bitmap uint32 words,
+    stats dict) as host arrays."""
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8))
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    tel = None
+    if edge_labels is not None:
+        tel = np.ascontiguousarray(np.asarray(edge_labels, dtype=np.uint8))
+        if tel.shape[0] != ed.shape[0] // 2:
+            raise ValueError("one edge label per template edge")
+    omega = np.zeros(max(graph.n, 1), dtype=np.uint64)
+    bits = np.zeros(max(graph.words, 1), dtype=np.uint32)
+    st = WideStats()
+    ctx.check(lib.ccpm_lcc_wide(ctx.h, graph.h, int(lab.shape[0]), _ptr(lab)[0], int(ed.shape[0] // 2),
+                                _ptr(ed)[0], None if tel is None else _ptr(tel)[0], _ptr(omega)[0],
+                                _ptr(bits)[0], 0, ctypes.byref(st)), "ccpm_lcc_wide")
+    stats = {k: getattr(st, k) for k, _ in st._fields_}
+    return omega[: graph.n], bits[: graph.words], stats
+
+
 def batch_tuning(graph) -> dict:
     """The batch autotuner's choices for `graph` (ccpm_graph_batch_tuning)."""
-    v = [ctypes.c_int(0) for _ in range(4)]
+    v = [ctypes.c_int(0) for _ in range(5)]
     ms = ctypes.c_double(0.0)
     lib.ccpm_graph_batch_tuning(graph.h, *[ctypes.byref(x) for x in v], ctypes.byref(ms))
-    return {"workers": v[0].value, "search_split": v[1].value, "short_rows": v[2].value,
-            "hub_degree": v[3].value, "slice_ms": ms.value}
+    return {"workers": v[0].value, "grid_share": v[1].value, "search_split": v[2].value,
+            "short_rows": v[3].value, "hub_degree": v[4].value, "slice_ms": ms.value}
 
 
 class Template:

@@ -69,10 +69,35 @@ struct Template {
     std::string err;
 };
 
-// glue between translation units (ccpm_kernels.cu, ccpm_mlp.cu)
+// glue between translation units (ccpm_kernels.cu, ccpm_mlp.cu, ccpm_wide.cu)
 int ctx_device(ccpm_ctx *ctx);
 void *ctx_stream_ptr(ccpm_ctx *ctx);
-int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stream);
+int ctx_num_sms(ccpm_ctx *ctx);
+int ctx_set_err(ccpm_ctx *ctx, int code, const char *msg);
+// device arrays of a loaded graph (el: edge labels, NULL if none were set)
+struct GraphView {
+    int64_t n, m;
+    const int64_t *rp;
+    const int32_t *col;
+    const uint8_t *lab;
+    const uint8_t *el;
+    ccpm_ctx *ctx;
+};
+GraphView graph_view(ccpm_graph *g);
+// Scoring scratch of one caller (a context, or the network's own public
+// forward call): device inputs and outputs plus pinned host staging, grown on
+// demand.  Each batch worker scores with its own, so concurrent workers share
+// only the network's parameters, which scoring only reads.
+struct MlpScratch {
+    float *dx = nullptr, *dy = nullptr;   // device [cap * CCPM_MLP_IN], [cap]
+    float *hx = nullptr, *hy = nullptr;   // pinned host staging of the same sizes
+    int cap = 0;
+};
+void mlp_scratch_free(MlpScratch &sc);
+// wait_ev (a cudaEvent_t, nullable): wait by polling it and yielding the
+// core (batch workers), instead of the runtime's spinning stream wait.
+int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stream, MlpScratch &sc,
+              void *wait_ev = nullptr);
 
 // host helpers (ccpm_host.cpp)
 int  template_build(Template &t, int n0, const uint8_t *labels, int m0, const int32_t *edges);

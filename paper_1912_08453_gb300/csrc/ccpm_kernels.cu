@@ -2303,16 +2303,19 @@ struct Workspace {
     int64_t piece_cap = 0;
     void *scan_tmp = nullptr;
     size_t scan_tmp_bytes = 0;
+    MlpScratch mlp;                  // scoring scratch of the learned order
 };
 
 struct ccpm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int num_sms = 0;
+    int num_sms = 0;                      // SMs this context sizes its grids for
+    int sm_total = 0;                     // SMs of the device
     std::string err;
     Workspace ws;                         // scratch of prunes issued on this context
     std::vector<ccpm_ctx *> workers;      // contexts of concurrent batch workers
+    cudaEvent_t wait_ev = nullptr;        // batch workers: waits poll this event and yield
 };
 
 struct ccpm_graph {
@@ -2327,11 +2330,13 @@ struct ccpm_graph {
     uint8_t *nlab = nullptr;
     std::mutex lrow_mu;           // concurrent batch workers build the grouped rows once
     int tuned_workers = 0;        // batch settings chosen by the autotuner (0: not tuned yet)
-    int tuned_split = 0, tuned_short = 0, tuned_hub = 0;
+    int tuned_split = 0, tuned_short = 0, tuned_hub = 0, tuned_share = 0;
     double tuned_ms = 0.0;        // the chosen setting's time on the tuning slice
     std::atomic<int> prunes{0};   // prunes started on this graph
     std::atomic<bool> lrows_ready{false};   // lcol/nlab built (read without the lock)
     uint8_t *elab = nullptr;      // label of each entry's neighbour, CSR order (built on first use)
+    uint8_t *edge_lab = nullptr;  // edge label of each entry (ccpm_graph_set_edge_labels), or none
+    bool edge_lab_borrowed = false;
 };
 
 struct ccpm_tmpl {
@@ -2354,6 +2359,19 @@ namespace {
 int set_err(ccpm_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
     return code;
+}
+
+// Wait for the work queued on the context's stream.  A batch worker polls an
+// event and yields its core between polls: the runtime's own wait spins, and
+// a dozen workers spinning at once would hold the host cores that the other
+// workers need to launch their next kernels (a worker whose GPU work is done
+// could then wait a scheduler time slice for a core).
+cudaError_t ctx_sync(ccpm_ctx *ctx) {
+    if (!ctx->wait_ev) return cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaEventRecord(ctx->wait_ev, ctx->stream);
+    if (e != cudaSuccess) return e;
+    while ((e = cudaEventQuery(ctx->wait_ev)) == cudaErrorNotReady) std::this_thread::yield();
+    return e;
 }
 
 // FNV-1a 64 over a byte range (fingerprints and the checksum of saved states)
@@ -2418,6 +2436,7 @@ void ws_free(Workspace &w) {
     for (int i = 0; i < 2; i++) { cudaFree(w.sub_nlab[i]); cudaFree(w.sub_dslot[i]); cudaFree(w.sub_gdir[i]); }
     cudaFree(w.slot_ctr);
     cudaFree(w.deg); cudaFree(w.piece_cnt); cudaFree(w.scan_tmp);
+    mlp_scratch_free(w.mlp);
     w = Workspace{};
 }
 
@@ -2539,7 +2558,7 @@ int expand_more(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int max_depth, int64
         CU(ctx, cudaGetLastError());
         unsigned int n2 = 0;
         CU(ctx, cudaMemcpyAsync(&n2, &w.st->n_items, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        CU(ctx, ctx_sync(ctx));
         if ((int64_t)n2 > w.items_cap) return set_err(ctx, CCPM_EOVERFLOW, "search items overflow");
         a.n_items = n2;
     }
@@ -2598,7 +2617,7 @@ int item_passes(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int kind, uint64_t s
         CU(ctx, cudaMemcpyAsync(&w.aux_h[1], &w.st->n_spill, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaMemcpyAsync(&w.aux_h[2], &w.st->overflow, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaMemcpyAsync(&w.aux_h[3], &w.st->spill_stop, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-        CU(ctx, cudaStreamSynchronize(s));
+        CU(ctx, ctx_sync(ctx));
         const unsigned int spilled = std::min((unsigned int)(w.aux_h[1] & 0xFFFFFFFFull),
                                               (unsigned int)(w.aux_h[3] & 0xFFFFFFFFull));
         const unsigned int over = (unsigned int)(w.aux_h[2] & 0xFFFFFFFFull);
@@ -2693,14 +2712,14 @@ struct Pipeline {
         CU(ctx, cudaGetLastError());
         CU(ctx, cudaMemcpyAsync(w.hist_h, w.hist, (kMaxT + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 ctx->stream));
-        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        CU(ctx, ctx_sync(ctx));
         return CCPM_OK;
     }
 
     int read_stats() {
         Workspace &w = ctx->ws;
         CU(ctx, cudaMemcpyAsync(w.st_h, w.st, sizeof(RoundStats), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        CU(ctx, ctx_sync(ctx));
         return CCPM_OK;
     }
 
@@ -2797,7 +2816,7 @@ struct Pipeline {
             CU(ctx, cudaEventRecord(w.ev[5], ctx->stream));
             CU(ctx, cudaMemcpyAsync(w.st_ring_h, w.st_ring, sizeof(RoundStats) * (size_t)G, cudaMemcpyDeviceToHost,
                                     ctx->stream));
-            CU(ctx, cudaStreamSynchronize(ctx->stream));
+            CU(ctx, ctx_sync(ctx));
             float ms = 0.f;
             CU(ctx, cudaEventElapsedTime(&ms, w.ev[4], w.ev[5]));
             ms_lcc_kernel += ms;
@@ -2918,12 +2937,14 @@ struct Pipeline {
         if (!w.sub_rp[nb] && (rc = dalloc(ctx, &w.sub_rp[nb], (size_t)g->n + 1))) return rc;
         if (!w.sub_dslot[nb] && (rc = dalloc(ctx, &w.sub_dslot[nb], (size_t)g->n))) return rc;
         if (!w.slot_ctr && (rc = dalloc(ctx, &w.slot_ctr, 1))) return rc;
+        // buffers grow to twice what is needed (a cudaFree waits for the whole
+        // device, which would stall every other worker of a batch)
         const int64_t dir_need = (n_small + n_med + n_chunk + 1) * (int64_t)(nl + 1);
         if (dir_need > w.gdir_cap[nb]) {
             cudaFree(w.sub_gdir[nb]);
             w.sub_gdir[nb] = nullptr;
             w.gdir_cap[nb] = 0;
-            const int64_t cap = std::max<int64_t>(dir_need, w.gdir_cap[nb ^ 1]);
+            const int64_t cap = std::max<int64_t>(2 * dir_need, w.gdir_cap[nb ^ 1]);
             if ((rc = dalloc(ctx, &w.sub_gdir[nb], (size_t)cap))) return rc;
             w.gdir_cap[nb] = cap;
         }
@@ -2936,7 +2957,7 @@ struct Pipeline {
             w.sub_nlab[nb] = nullptr;
             w.sub_bits[nb] = nullptr;
             w.sub_cap[nb] = 0;
-            const int64_t cap = std::max<int64_t>(need, w.sub_cap[nb ^ 1]);
+            const int64_t cap = std::max<int64_t>(std::min<int64_t>(2 * need, g->m + 64), w.sub_cap[nb ^ 1]);
             if ((rc = dalloc(ctx, &w.sub_col[nb], (size_t)cap))) return rc;
             if ((rc = dalloc(ctx, &w.sub_nlab[nb], (size_t)cap))) return rc;
             if ((rc = dalloc(ctx, &w.sub_bits[nb], (size_t)(cap / 32 + 2)))) return rc;
@@ -3019,6 +3040,19 @@ struct Pipeline {
 namespace ccpm {
 int ctx_device(ccpm_ctx *ctx) { return ctx->device; }
 void *ctx_stream_ptr(ccpm_ctx *ctx) { return (void *)ctx->stream; }
+int ctx_num_sms(ccpm_ctx *ctx) { return ctx->num_sms; }
+int ctx_set_err(ccpm_ctx *ctx, int code, const char *msg) { return set_err(ctx, code, msg); }
+GraphView graph_view(ccpm_graph *g) {
+    GraphView v;
+    v.n = g->n;
+    v.m = g->m;
+    v.rp = g->rp;
+    v.col = g->col;
+    v.lab = g->lab;
+    v.el = g->edge_lab;
+    v.ctx = g->ctx;
+    return v;
+}
 }  // namespace ccpm
 
 extern "C" {
@@ -3042,6 +3076,7 @@ int ccpm_ctx_create(int device, void *stream, ccpm_ctx_t *out) {
     c->device = device;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->sm_total = c->num_sms;
     if (e == cudaSuccess) {
         if (stream) {
             c->stream = (cudaStream_t)stream;
@@ -3063,6 +3098,7 @@ void ccpm_ctx_destroy(ccpm_ctx_t c) {
     cudaSetDevice(c->device);
     for (ccpm_ctx *wk : c->workers) ccpm_ctx_destroy(wk);
     ws_free(c->ws);
+    if (c->wait_ev) cudaEventDestroy(c->wait_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -3151,7 +3187,46 @@ void ccpm_graph_destroy(ccpm_graph_t g) {
     cudaFree(g->lcol);
     cudaFree(g->nlab);
     cudaFree(g->elab);
+    if (!g->edge_lab_borrowed) cudaFree(g->edge_lab);
     delete g;
+}
+
+int ccpm_graph_set_edge_labels(ccpm_graph_t g, const uint8_t *edge_labels, int flags) {
+    if (!g) return CCPM_EINVAL;
+    ccpm_ctx *ctx = g->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    const bool dev = (flags & CCPM_DEVICE_PTRS) != 0;
+    if (edge_labels && (flags & CCPM_VALIDATE)) {
+        if (dev) return set_err(ctx, CCPM_EINVAL, "edge labels: CCPM_VALIDATE needs host pointers");
+        // both entries of every edge carry the same label
+        std::vector<int64_t> rp((size_t)g->n + 1);
+        std::vector<int32_t> col((size_t)g->m);
+        CU(ctx, cudaMemcpy(rp.data(), g->rp, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
+        if (g->m > 0) CU(ctx, cudaMemcpy(col.data(), g->col, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost));
+        for (int64_t v = 0; v < g->n; v++)
+            for (int64_t e = rp[(size_t)v]; e < rp[(size_t)v + 1]; e++) {
+                const int32_t u = col[(size_t)e];
+                const int32_t *lo = col.data() + rp[(size_t)u], *hi = col.data() + rp[(size_t)u + 1];
+                const int32_t *f = std::lower_bound(lo, hi, (int32_t)v);
+                if (f == hi || *f != v) return set_err(ctx, CCPM_EINVAL, "edge labels: missing reverse entry");
+                if (edge_labels[(size_t)(f - col.data())] != edge_labels[(size_t)e])
+                    return set_err(ctx, CCPM_EINVAL, "edge labels: the two entries of an edge differ");
+            }
+    }
+    if (!g->edge_lab_borrowed) cudaFree(g->edge_lab);
+    g->edge_lab = nullptr;
+    g->edge_lab_borrowed = false;
+    if (!edge_labels) return CCPM_OK;
+    if (dev) {
+        g->edge_lab = const_cast<uint8_t *>(edge_labels);
+        g->edge_lab_borrowed = true;
+        return CCPM_OK;
+    }
+    int rc = dalloc(ctx, &g->edge_lab, (size_t)std::max<int64_t>(g->m, 1));
+    if (rc) return rc;
+    if (g->m > 0) CU(ctx, cudaMemcpyAsync(g->edge_lab, edge_labels, (size_t)g->m, cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return CCPM_OK;
 }
 
 int ccpm_tmpl_load(ccpm_ctx_t ctx, int n0, const uint8_t *labels, int m0, const int32_t *edges, ccpm_tmpl_t *out) {
@@ -3403,7 +3478,8 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                 // expensive checks wait for a state that cheaper ones have shrunk
                 std::vector<float> score(remaining.size());
                 P.launches++;
-                RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s));
+                RCF(mlp_score(opt.mlp, (int)remaining.size(), feats.data(), score.data(), (void *)s, w.mlp,
+                               (void *)ctx->wait_ev));
                 for (size_t i = 1; i < remaining.size(); i++)
                     if (score[i] > score[0] + 1.f && score[i] > score[pick]) pick = i;
             }
@@ -3506,7 +3582,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
         r->phase_rounds.push_back((int32_t)rr);
         total_rounds += rr;
         if (changed) RCF(P.omega_hist());      // state for the next decision
-        else CUF(cudaStreamSynchronize(s));
+        else CUF(ctx_sync(ctx));
         float ms_a = 0.f, ms_b = 0.f;
         cudaEventElapsedTime(&ms_a, w.ev[6], w.ev[7]);
         cudaEventElapsedTime(&ms_b, w.ev[7], w.ev[8]);
@@ -3736,11 +3812,11 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                 a.n_roots = n_roots;
             }
             CUF(cudaEventRecord(fev[3], s));
-            CUF(cudaStreamSynchronize(s));
+            CUF(ctx_sync(ctx));
             cudaEventElapsedTime(&ms_fv, fev[1], fev[2]);
             cudaEventElapsedTime(&ms_fe, fev[2], fev[3]);
         } else {
-            CUF(cudaStreamSynchronize(s));
+            CUF(ctx_sync(ctx));
         }
         cudaEventElapsedTime(&ms_fc, fev[0], fev[1]);
         final_done = true;
@@ -3766,7 +3842,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
     k_count<<<grid_for(ctx, std::max<int64_t>(g->n, w.words), 256, 8), 256, 0, s>>>(g->n, r->om, w.words, r->eb, w.cnt);
     CUF(cudaGetLastError());
     CUF(cudaMemcpyAsync(w.cnt_h, w.cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CUF(cudaStreamSynchronize(s));
+    CUF(ctx_sync(ctx));
     float ms_lcc = 0, ms_nlcc = 0, ms_final = 0;
     cudaEventElapsedTime(&ms_lcc, w.ev[0], w.ev[1]);
     cudaEventElapsedTime(&ms_nlcc, w.ev[1], w.ev[2]);
@@ -3815,22 +3891,35 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
 #undef RCF
 }
 
-// Run templates [lo, hi) of a batch on `W` worker contexts, one host thread
-// each, taking templates from a shared counter.  Returns the first error.
-static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, int lo, int hi, const ccpm_tmpl_t *tmpls,
+// Run the templates tmpls[order[0..)] of a batch on `W` worker contexts, one
+// host thread each, taking templates from a shared counter in that order.
+// Returns the first error.
+static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, const std::vector<int> &order, const ccpm_tmpl_t *tmpls,
                      const ccpm_options *opt, ccpm_result_t *outs, int W, int *budget_hit) {
+    const int hi = (int)order.size();
+    W = std::max(1, std::min(W, hi));
     while ((int)ctx->workers.size() < W) {
         ccpm_ctx *wk = nullptr;
         int rc = ccpm_ctx_create(ctx->device, nullptr, &wk);
         if (rc) return set_err(ctx, rc, "batch: worker context");
         ctx->workers.push_back(wk);
+        if (cudaEventCreateWithFlags(&wk->wait_ev, cudaEventDisableTiming) != cudaSuccess)
+            return set_err(ctx, CCPM_ECUDA, "batch: worker event");
+    }
+    // grid share: a worker sizes its grids for 1/share of the SMs (the
+    // persistent-style search kernels would otherwise hold every SM until they
+    // finish, and the small kernels of other templates would wait behind them)
+    const int share = std::max(1, opt->grid_share);
+    for (int i = 0; i < W; i++) {
+        ccpm_ctx *wk = ctx->workers[(size_t)i];
+        wk->num_sms = std::max(1, wk->sm_total / share);
     }
     // workers start after everything already queued on the caller's stream
     cudaEvent_t ready;
     CU(ctx, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     CU(ctx, cudaEventRecord(ready, ctx->stream));
     for (int i = 0; i < W; i++) CU(ctx, cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
-    std::atomic<int> next(lo);
+    std::atomic<int> next(0);
     std::atomic<int> first_err(0);
     std::atomic<int> budget(0);
     std::mutex err_mu;
@@ -3840,8 +3929,9 @@ static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, int lo, int hi, const ccpm_tm
         ccpm_ctx *wk = ctx->workers[(size_t)i];
         pool.emplace_back([&, wk]() {
             cudaSetDevice(wk->device);
-            for (int k = next.fetch_add(1); k < hi; k = next.fetch_add(1)) {
+            for (int i = next.fetch_add(1); i < hi; i = next.fetch_add(1)) {
                 if (first_err.load()) break;
+                const int k = order[(size_t)i];
                 int rc = ccpm_prune(wk, g, tmpls[k], opt, &outs[k]);
                 if (rc == CCPM_EBUDGET) {
                     budget.store(1);
@@ -3889,24 +3979,35 @@ int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *t
         // windows a search scans before it hands work on, then the row length
         // of the flat short-row path, then the piece length of long rows.  The
         // choice is kept on the graph.
-        const int slice = std::max(1, std::min(T, 8));
+        // the slice: 32 templates spread evenly over the batch (long enough
+        // for workers to queue, as they do on the whole batch)
+        const int slice = std::max(1, std::min(T, 32));
+        std::vector<int> sl;
+        for (int i = 0; i < slice; i++) sl.push_back((int)((int64_t)i * T / slice));
         ccpm_options cand = opt;
         cand.search_split = 0;
         cand.short_rows = 0;
         cand.hub_degree = 0;
+        cand.grid_share = 1;
         int best_w = 8;
         double best = 1e300;
         auto time_slice = [&](const ccpm_options &o, int W, double &ms) -> int {
             auto t0 = std::chrono::steady_clock::now();
-            int rc2 = run_batch(ctx, g, 0, slice, tmpls, &o, outs, std::min(W, slice), &budget_hit);
+            int rc2 = run_batch(ctx, g, sl, tmpls, &o, outs, W, &budget_hit);
             ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             return rc2;
         };
         double ms = 0;
         int rc;
-        for (int Wc : {4, 8, 16}) {
+        for (int Wc : {1, 2, 4, 8, 16}) {
             if ((rc = time_slice(cand, Wc, ms))) return rc;
             if (ms < best) { best = ms; best_w = Wc; }
+        }
+        for (int gs : {2, 4}) {
+            ccpm_options o = cand;
+            o.grid_share = gs;
+            if ((rc = time_slice(o, best_w, ms))) return rc;
+            if (ms < best) { best = ms; cand.grid_share = gs; }
         }
         for (int sp : {512, 8192}) {
             ccpm_options o = cand;
@@ -3930,6 +4031,7 @@ int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *t
         g->tuned_split = cand.search_split;
         g->tuned_short = cand.short_rows;
         g->tuned_hub = cand.hub_degree;
+        g->tuned_share = cand.grid_share;
         g->tuned_ms = best;
     }
     int W = opt.batch_workers > 0 ? opt.batch_workers : g->tuned_workers;
@@ -3938,9 +4040,19 @@ int ccpm_prune_batch(ccpm_ctx_t ctx, ccpm_graph_t g, int T, const ccpm_tmpl_t *t
         if (opt.search_split == 0) opt.search_split = g->tuned_split;
         if (opt.short_rows == 0) opt.short_rows = g->tuned_short;
         if (opt.hub_degree == 0) opt.hub_degree = g->tuned_hub;
+        if (opt.grid_share == 0) opt.grid_share = g->tuned_share;
     }
     if (T > 0) {
-        int rc = run_batch(ctx, g, 0, T, tmpls, &opt, outs, std::min(W, T), &budget_hit);
+        // longest first when the results of an earlier call give each
+        // template's time (the tail of the batch is then short templates)
+        std::vector<int> order(T);
+        for (int i = 0; i < T; i++) order[(size_t)i] = i;
+        bool timed = true;
+        for (int i = 0; i < T && timed; i++) timed = outs[i] && outs[i]->counts.ms_total > 0.0;
+        if (timed)
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int x, int y) { return outs[x]->counts.ms_total > outs[y]->counts.ms_total; });
+        int rc = run_batch(ctx, g, order, tmpls, &opt, outs, W, &budget_hit);
         if (rc) return rc;
     }
     if (budget_hit) return set_err(ctx, CCPM_EBUDGET, "a search budget was exceeded in the batch");
@@ -4300,10 +4412,11 @@ const uint32_t *ccpm_result_edge_bitmap_device(ccpm_result_t r) { return r ? r->
 
 int ccpm_graph_batch_workers(ccpm_graph_t g) { return g ? g->tuned_workers : 0; }
 
-int ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *search_split, int *short_rows, int *hub_degree,
-                            double *slice_ms) {
+int ccpm_graph_batch_tuning(ccpm_graph_t g, int *workers, int *grid_share, int *search_split, int *short_rows,
+                            int *hub_degree, double *slice_ms) {
     if (!g) return CCPM_EINVAL;
     if (workers) *workers = g->tuned_workers;
+    if (grid_share) *grid_share = g->tuned_share;
     if (search_split) *search_split = g->tuned_split;
     if (short_rows) *short_rows = g->tuned_short;
     if (hub_degree) *hub_degree = g->tuned_hub;

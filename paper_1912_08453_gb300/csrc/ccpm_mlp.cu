@@ -20,6 +20,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ccpm_internal.h"
@@ -286,10 +287,9 @@ struct ccpm_mlp {
     cudaStream_t stream = nullptr;
     float *prm = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *sse = nullptr;
     int adam_step = 0;
-    // scoring scratch kept between calls (the pipeline scores before every constraint)
-    float *sx = nullptr, *sy = nullptr;
-    int s_cap = 0;
-    std::mutex mu;               // batch workers may score concurrently
+    // scratch of the public forward call (pipelines score with their context's own)
+    ccpm::MlpScratch own;
+    std::mutex mu;               // public forward calls may come from several threads
 };
 
 namespace {
@@ -298,7 +298,10 @@ size_t fwd_smem() { return sizeof(FwdSmem); }
 size_t bwd_smem() { return sizeof(BwdSmem); }
 
 int configure_kernels() {
+    // batch workers reach this concurrently: configure once, under a lock
+    static std::mutex mu;
     static bool done = false;
+    std::lock_guard<std::mutex> lock(mu);
     if (done) return CCPM_OK;
     if (cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem()) != cudaSuccess)
         return CCPM_ECUDA;
@@ -321,31 +324,49 @@ int tiles(int B) { return (B + ROWS - 1) / ROWS; }
 
 namespace ccpm {
 
-// Forward pass for the pruning pipeline's ordering decisions (host arrays).
-int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stream) {
+void mlp_scratch_free(MlpScratch &sc) {
+    cudaFree(sc.dx);
+    cudaFree(sc.dy);
+    if (sc.hx) cudaFreeHost(sc.hx);
+    if (sc.hy) cudaFreeHost(sc.hy);
+    sc = MlpScratch{};
+}
+
+// Forward pass for the pruning pipeline's ordering decisions (host arrays),
+// with the caller's scratch: no lock is held while the GPU works, so batch
+// workers that score at the same time do not wait for one another.
+int mlp_score(ccpm_mlp *m, int B, const float *host_x, float *host_y, void *stream, MlpScratch &sc, void *wait_ev) {
     cudaStream_t s = (cudaStream_t)stream;
     if (!m || B <= 0) return CCPM_EINVAL;
     if (configure_kernels()) return CCPM_ECUDA;
-    std::lock_guard<std::mutex> lock(m->mu);
-    if (B > m->s_cap) {
-        cudaFree(m->sx);
-        cudaFree(m->sy);
-        m->sx = m->sy = nullptr;
+    if (B > sc.cap) {
+        mlp_scratch_free(sc);
         const int cap = std::max(B, 256);
-        if (cudaMalloc(&m->sx, sizeof(float) * (size_t)cap * IN) != cudaSuccess ||
-            cudaMalloc(&m->sy, sizeof(float) * (size_t)cap) != cudaSuccess) {
-            m->s_cap = 0;
+        if (cudaMalloc(&sc.dx, sizeof(float) * (size_t)cap * IN) != cudaSuccess ||
+            cudaMalloc(&sc.dy, sizeof(float) * (size_t)cap) != cudaSuccess ||
+            cudaMallocHost(&sc.hx, sizeof(float) * (size_t)cap * IN) != cudaSuccess ||
+            cudaMallocHost(&sc.hy, sizeof(float) * (size_t)cap) != cudaSuccess) {
+            mlp_scratch_free(sc);
             return CCPM_ENOMEM;
         }
-        m->s_cap = cap;
+        sc.cap = cap;
     }
-    cudaError_t e = cudaMemcpyAsync(m->sx, host_x, sizeof(float) * (size_t)B * IN, cudaMemcpyHostToDevice, s);
+    std::memcpy(sc.hx, host_x, sizeof(float) * (size_t)B * IN);
+    cudaError_t e = cudaMemcpyAsync(sc.dx, sc.hx, sizeof(float) * (size_t)B * IN, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        k_mlp_forward<<<tiles(B), THREADS, fwd_smem(), s>>>(m->prm, m->sx, B, m->sy);
+        k_mlp_forward<<<tiles(B), THREADS, fwd_smem(), s>>>(m->prm, sc.dx, B, sc.dy);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_y, m->sy, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc.hy, sc.dy, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && wait_ev) {
+        cudaEvent_t ev = (cudaEvent_t)wait_ev;
+        e = cudaEventRecord(ev, s);
+        if (e == cudaSuccess)
+            while ((e = cudaEventQuery(ev)) == cudaErrorNotReady) std::this_thread::yield();
+    } else if (e == cudaSuccess) {
+        e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess) std::memcpy(host_y, sc.hy, sizeof(float) * (size_t)B);
     return e == cudaSuccess ? CCPM_OK : CCPM_ECUDA;
 }
 
@@ -397,7 +418,7 @@ void ccpm_mlp_destroy(ccpm_mlp_t m) {
     if (!m) return;
     cudaSetDevice(m->device);
     cudaFree(m->prm); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->sse);
-    cudaFree(m->sx); cudaFree(m->sy);
+    ccpm::mlp_scratch_free(m->own);
     delete m;
 }
 
@@ -424,7 +445,8 @@ int ccpm_mlp_get_params(ccpm_mlp_t m, float *host_params) {
 int ccpm_mlp_forward(ccpm_mlp_t m, int B, const float *host_x, float *host_y) {
     if (!m || B <= 0 || !host_x || !host_y) return CCPM_EINVAL;
     if (cudaSetDevice(m->device) != cudaSuccess) return CCPM_ECUDA;
-    return mlp_score(m, B, host_x, host_y, (void *)m->stream);
+    std::lock_guard<std::mutex> lock(m->mu);
+    return mlp_score(m, B, host_x, host_y, (void *)m->stream, m->own);
 }
 
 int ccpm_mlp_gradient(ccpm_mlp_t m, int B, const float *host_x, const float *host_t, float *host_grad,

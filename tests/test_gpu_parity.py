@@ -205,12 +205,14 @@ def test_batch_equals_one_at_a_time(ctx):
     tmpls = [base] + wl.edit_variants(base, 11, seed=3, label_pool=pool, n_min=4, n_max=8)
     graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
     hs = [ccpm.Template(ctx, t.labels, t.edges) for t in tmpls]
-    for workers in (0, 3):
-        res = ccpm.prune_batch(ctx, graph, hs, ccpm.options(batch_workers=workers))
+    # autotuned; then three workers whose grids use a quarter of the SMs each
+    for workers, share in ((0, 0), (3, 4)):
+        res = ccpm.prune_batch(ctx, graph, hs, ccpm.options(batch_workers=workers, grid_share=share))
         if workers == 0:
             # the autotuner chose and recorded every setting it tunes
             tune = ccpm.batch_tuning(graph)
-            assert tune["workers"] in (4, 8, 16) and tune["search_split"] in (0, 512, 8192)
+            assert tune["workers"] in (1, 2, 4, 8, 16) and tune["grid_share"] in (1, 2, 4)
+            assert tune["search_split"] in (0, 512, 8192)
             assert tune["short_rows"] in (0, 32, 256) and tune["hub_degree"] in (0, 4096)
             assert tune["slice_ms"] > 0
         for t, h, r in zip(tmpls, hs, res):
