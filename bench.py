@@ -85,6 +85,11 @@ WORKLOADS = {
                 "templates": {}, "lcc_templates": {"c3_5cycle8_frequent": C3_FREQUENT}},
     "c4base22": {"name": "c4-base-rmat22-zipf", "scale": 22, "labels": "zipf", "gen": "philox",
                  "templates": {"c4_base": C4_BASE}},
+    # f3: LCC for a 48-vertex template with edge labels (64-bit omega words),
+    # scale 22, degree labels, three edge labels (weights 8:1:1); the template
+    # is a breadth-first sample of the graph itself, so it matches
+    "f3": {"name": "f3-wide-rmat22-degree-el3", "scale": 22, "labels": "degree", "gen": "philox",
+           "wide": {"n0": 48, "extra": 6, "seed": 48, "n_edge_labels": 3, "weights": [8, 1, 1]}},
     "rmat16-degree": {"name": "rmat16-degree", "scale": 16, "labels": "degree", "gen": "numpy",
                       "templates": {"treetri6": ([5, 4, 8, 7, 4, 5],
                                                  [(0, 1), (1, 2), (1, 3), (3, 4), (3, 5), (2, 3)])}},
@@ -442,6 +447,46 @@ def single_template_line(args, cfg, ctx, stream, local, reps=2):
     return out
 
 
+def wide_line(args, cfg, ctx, stream, local, reps=3):
+    """ccpm_lcc_wide on an edge-labelled graph: time, rounds and the roofline.
+    Algorithmic bytes per round, by the same accounting as the 32-bit LCC:
+    13.25 per active entry (4 column, 8 neighbour omega, 1 edge label, 1/4
+    edge bit) and 24 per active vertex (8 offsets, 16 own omega read and
+    written)."""
+    import torch
+    from paper_1912_08453_gb300 import ccpm
+    from paper_1912_08453_gb300 import workloads as wl
+    t0 = time.time()
+    g = make_graph(cfg, device=f"cuda:{local}")
+    w = cfg["wide"]
+    el = wl.edge_labels(g.row_ptr, g.col, w["n_edge_labels"], seed=w["seed"], weights=w["weights"])
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    h = host_graph(g)
+    tl, te, tel = wl.sampled_template(h, el.cpu().numpy(), w["n0"], w["extra"], seed=w["seed"])
+    del h
+    graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
+    graph.set_edge_labels(el)
+    ccpm.lcc_wide(ctx, graph, tl, te, tel)              # warm-up
+    stats = []
+    for _ in range(reps):
+        _, _, st = ccpm.lcc_wide(ctx, graph, tl, te, tel)
+        stats.append(st)
+    st = stats[-1]
+    ms = statistics.median(x["ms"] for x in stats)
+    alg = 13.25 * st["edges_scanned"] + 24.0 * st["vertices_scanned"]
+    out = {"workload": cfg["name"], "n": g.n, "m_dir": g.m_dir, "gen_s": gen_s, "n0": len(tl), "m0": len(te),
+           "edge_labels_in_template": len(set(tel)), "ms": ms, "rounds": st["rounds"],
+           "active_v_fixpoint": st["active_v"], "active_e_fixpoint": st["active_e_dir"],
+           "roofline": roofline("k_wide_round", alg, ms, st["rounds"], cfg["name"],
+                                {"M_a": st["edges_scanned"], "n_a": st["vertices_scanned"],
+                                 "note": "device time of the whole call (init, rounds, hand-back) per round"})}
+    graph.close()
+    del g, el
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_c4(args, cfg):
     import torch
     from paper_1912_08453_gb300.build import build
@@ -557,7 +602,16 @@ def run_c4(args, cfg):
 
     e2e = None
     if not args.no_e2e and world == 1:
-        e2e = run_c4_e2e(args, ctx, g, hs, learned, stream)
+        # every e2e step loads the graph anew: it runs with the settings the
+        # autotuner chose on the resident graph (a user keeps them the same way)
+        tune = ccpm.batch_tuning(graph)
+        e2e_opt = ccpm.Options.from_buffer_copy(learned)
+        e2e_opt.batch_workers = tune["workers"]
+        e2e_opt.grid_share = tune["grid_share"]
+        e2e_opt.search_split = tune["search_split"]
+        e2e_opt.short_rows = tune["short_rows"]
+        e2e_opt.hub_degree = tune["hub_degree"]
+        e2e = run_c4_e2e(args, ctx, g, hs, e2e_opt, stream)
 
     cpu = None
     oracle_parity = None
@@ -581,6 +635,7 @@ def run_c4(args, cfg):
     if not args.no_extras and world == 1:
         extras["c3"] = single_template_line(args, WORKLOADS["c3"], ctx, stream, local)
         extras["c2"] = single_template_line(args, WORKLOADS["c2"], ctx, stream, local, reps=3)
+        extras["f3"] = wide_line(args, WORKLOADS["f3"], ctx, stream, local)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank != 0:
@@ -861,6 +916,21 @@ def run_single(args, cfg):
     ctx = ccpm.Context(local, stream=stream.cuda_stream)
     clocks = ClockSampler(local)
     clocks.start()
+    if "wide" in cfg:
+        out = wide_line(args, cfg, ctx, stream, local, reps=max(args.steps, 1))
+        clk = clocks.stop()
+        if rank != 0:
+            return
+        roof = out["roofline"]
+        line = {"metric": METRIC, "value": roof["M_a"] / (out["ms"] / 1e3) if out["ms"] else 0.0,
+                "unit": "edges scanned/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": out["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u64", "data": "synthetic", "config": {"workload": cfg["name"], "n": out["n"],
+                                                                "m_dir": out["m_dir"]},
+                "roofline": roof, "detail": out, "clocks": clk, "cpu_baseline": None, "e2e": None,
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+        return
     out = single_template_line(args, cfg, ctx, stream, local, reps=max(args.steps, 1))
     clk = clocks.stop()
     if rank != 0:

@@ -423,6 +423,7 @@ int  ccpm_graph_set_edge_labels(ccpm_graph_t g, const uint8_t *edge_labels, int 
 typedef struct {
     int64_t rounds;          /* LCC rounds executed, the final quiescent one included */
     int64_t edges_scanned;   /* active entries read, summed over the rounds           */
+    int64_t vertices_scanned;/* active vertices read, summed over the rounds          */
     int64_t active_v;        /* vertices whose omega is not empty at the fixpoint     */
     int64_t active_e_dir;    /* CSR entries whose bit is set at the fixpoint          */
     double  ms;              /* device time of the call (events on the ctx stream)    */

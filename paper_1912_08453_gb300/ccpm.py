@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
 
 
 class WideStats(ctypes.Structure):
-    _fields_ = [("rounds", ctypes.c_int64), ("edges_scanned", ctypes.c_int64), ("active_v", ctypes.c_int64),
+    _fields_ = [("rounds", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
+                ("vertices_scanned", ctypes.c_int64), ("active_v", ctypes.c_int64),
                 ("active_e_dir", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 

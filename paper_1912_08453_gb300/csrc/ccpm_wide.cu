@@ -55,6 +55,7 @@ struct __align__(16) WideTab {
 struct WideCounters {
     unsigned long long n_next;     // vertices listed for the next round
     unsigned long long scanned;    // active entries read (both ends live, bit set)
+    unsigned long long alive;      // active vertices read
     unsigned long long active_v, active_e;   // hand-back totals
     unsigned int changed;
     unsigned int pad;
@@ -131,7 +132,7 @@ k_wide_round(WideArgs a) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int n_el = T.n_el, n_cls = T.n_cls;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, alive = 0;
     unsigned int changed = 0;
     for (int64_t i = gw; i < a.n_in; i += nw) {
         const int32_t v = a.list_in[i];
@@ -141,6 +142,7 @@ k_wide_round(WideArgs a) {
             if (lane == 0) a.om_out[v] = 0;
             continue;
         }
+        if (lane == 0) alive++;
         // template neighbours of omega(v) per edge-label index
         uint64_t nb[kWEL];
 #pragma unroll
@@ -160,38 +162,56 @@ k_wide_round(WideArgs a) {
 #pragma unroll
         for (int j = 0; j < kWEL; j++) U[j] = 0;
         uint32_t nN = 0, achg = 0;
-        for (int64_t w0 = beg >> 5; (w0 << 5) < end; w0++) {
-            const int64_t e = (w0 << 5) + lane;
-            const uint32_t word = a.ebits[w0];
-            const bool bit = e >= beg && e < end && ((word >> lane) & 1u);
-            uint64_t wu = 0;
-            int j = 0xFF;
-            if (bit) {
-                wu = a.om_in[a.col[e]];
-                j = T.el_index[a.el ? a.el[e] : 0];
-            }
-            uint64_t m = 0;
+        // four windows per step: their bits, columns, edge labels and
+        // neighbour omegas are all loaded before any of them is used
+        constexpr int WU = 4;
+        for (int64_t w0 = beg >> 5; (w0 << 5) < end; w0 += WU) {
+            bool bit[WU];
+            int32_t u[WU];
+            uint8_t lb[WU];
+            uint64_t wn[WU];
 #pragma unroll
-            for (int jj = 0; jj < kWEL; jj++)
-                if (j == jj) m = nb[jj];
-            const bool live = bit && wu != 0;      // both ends active: the entry is active
-            const bool pass = live && (wu & m) != 0;
-            scanned += live ? 1ull : 0ull;
-            if (live && !pass) achg = 1;            // eta eliminates an active entry
-            if (pass) {
-                nN++;
+            for (int k = 0; k < WU; k++) {
+                const int64_t e = ((w0 + k) << 5) + lane;
+                const uint32_t word = ((w0 + k) << 5) < end ? a.ebits[w0 + k] : 0u;
+                bit[k] = e >= beg && e < end && ((word >> lane) & 1u);
+            }
+#pragma unroll
+            for (int k = 0; k < WU; k++) {
+                const int64_t e = ((w0 + k) << 5) + lane;
+                u[k] = bit[k] ? a.col[e] : 0;
+                lb[k] = (bit[k] && a.el) ? a.el[e] : (uint8_t)0;
+            }
+#pragma unroll
+            for (int k = 0; k < WU; k++) wn[k] = bit[k] ? a.om_in[u[k]] : 0ull;
+#pragma unroll
+            for (int k = 0; k < WU; k++) {
+                if (((w0 + k) << 5) >= end) break;          // past the row (warp-uniform)
+                const uint64_t wu = wn[k];
+                const int j = bit[k] ? (int)T.el_index[lb[k]] : 0xFF;
+                uint64_t m = 0;
 #pragma unroll
                 for (int jj = 0; jj < kWEL; jj++)
-                    if (j == jj) U[jj] |= wu;
-            }
-            // the bit goes with the failing entries and with those whose other
-            // end is inactive already (no change: that entry is inactive)
-            const uint32_t drop = __ballot_sync(FULL, bit && !pass);
-            if (drop && lane == 0) atomicAnd(&a.ebits[w0], ~drop);
-            for (int c = 0; c < n_cls; c++) {
-                if (!((wv >> T.cls_q[c]) & 1ull)) continue;
-                const uint32_t hit = __ballot_sync(FULL, pass && j == (int)T.cls_j[c] && (wu & T.cls_mask[c]) != 0);
-                if (lane == 0) cnt[wib][c] += (uint32_t)__popc(hit);
+                    if (j == jj) m = nb[jj];
+                const bool live = bit[k] && wu != 0;     // both ends active: the entry is active
+                const bool pass = live && (wu & m) != 0;
+                scanned += live ? 1ull : 0ull;
+                if (live && !pass) achg = 1;             // eta eliminates an active entry
+                if (pass) {
+                    nN++;
+#pragma unroll
+                    for (int jj = 0; jj < kWEL; jj++)
+                        if (j == jj) U[jj] |= wu;
+                }
+                // the bit goes with the failing entries and with those whose
+                // other end is inactive already (no change: that entry is inactive)
+                const uint32_t drop = __ballot_sync(FULL, bit[k] && !pass);
+                if (drop && lane == 0) atomicAnd(&a.ebits[w0 + k], ~drop);
+                for (int c = 0; c < n_cls; c++) {
+                    if (!((wv >> T.cls_q[c]) & 1ull)) continue;
+                    const uint32_t hit = __ballot_sync(FULL, pass && j == (int)T.cls_j[c] && (wu & T.cls_mask[c]) != 0);
+                    if (lane == 0) cnt[wib][c] += (uint32_t)__popc(hit);
+                }
             }
         }
 #pragma unroll
@@ -224,6 +244,7 @@ k_wide_round(WideArgs a) {
     scanned = warp_sum64(scanned);
     if (lane == 0) {
         if (scanned) atomicAdd(&a.st->scanned, scanned);
+        if (alive) atomicAdd(&a.st->alive, alive);
         if (changed) atomicOr(&a.st->changed, 1u);
     }
 }
@@ -411,7 +432,7 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
     WCU(cudaMemcpyAsync(B.st_h, B.st, sizeof(WideCounters), cudaMemcpyDeviceToHost, s), "copy");
     WCU(cudaStreamSynchronize(s), "sync");
     int64_t n_in = (int64_t)B.st_h->n_next;
-    int64_t rounds = 0, scanned = 0;
+    int64_t rounds = 0, scanned = 0, alive = 0;
     int cur = 0, li = 0;
     for (;;) {
         WCU(cudaMemsetAsync(B.st, 0, sizeof(WideCounters), s), "memset");
@@ -433,6 +454,7 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
         WCU(cudaStreamSynchronize(s), "sync");
         rounds++;
         scanned += (int64_t)B.st_h->scanned;
+        alive += (int64_t)B.st_h->alive;
         cur ^= 1;                  // omega of the round just run
         li ^= 1;
         n_in = (int64_t)B.st_h->n_next;
@@ -453,6 +475,7 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
         cudaEventElapsedTime(&ms, B.ev[0], B.ev[1]);
         stats->rounds = rounds;
         stats->edges_scanned = scanned;
+        stats->vertices_scanned = alive;
         stats->active_v = (int64_t)B.st_h->active_v;
         stats->active_e_dir = (int64_t)B.st_h->active_e;
         stats->ms = ms;

@@ -176,35 +176,70 @@ def graph_from_edge_list(n: int, edges, labels) -> Graph:
     return Graph(n, row_ptr, col, np.asarray(labels, dtype=np.uint8))
 
 
-def edge_labels(row_ptr: np.ndarray, col: np.ndarray, n_labels: int, seed: int = 3,
-                weights=None) -> np.ndarray:
+def edge_labels(row_ptr, col, n_labels: int, seed: int = 3, weights=None):
     """One label per undirected edge, the same on both of its CSR entries:
-    edge {x, y} (x < y) draws from a Philox stream keyed by the edge, so the
+    edge {x, y} (x < y) draws Philox4x32-10 with counter (y, x, 0, 0), so the
     two directions agree without a lookup.  `weights` (optional) skews the
-    distribution over 0..n_labels-1.  Returns uint8 [m_dir] in entry order."""
-    rp = np.asarray(row_ptr, dtype=np.int64)
-    c = np.asarray(col, dtype=np.int64)
-    n = rp.shape[0] - 1
-    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
-    lo, hi = np.minimum(src, c), np.maximum(src, c)
-    key = (lo.astype(np.uint64) << np.uint64(32)) | hi.astype(np.uint64)
-    u = _edge_uniform(key, seed)
-    if weights is None:
-        return (np.floor(u * n_labels).astype(np.int64) % n_labels).astype(np.uint8)
-    w = np.asarray(weights, dtype=np.float64)
-    cdf = np.cumsum(w / w.sum())
-    return np.minimum(np.searchsorted(cdf, u, side="right"), n_labels - 1).astype(np.uint8)
-
-
-def _edge_uniform(key: np.ndarray, seed: int) -> np.ndarray:
-    """Uniform [0, 1) per 64-bit key: Philox4x32-10 with the key as counter."""
+    distribution over 0..n_labels-1.  Numpy arrays in, a uint8 numpy array
+    out; torch tensors in, a uint8 tensor out on their device (same values)."""
     import torch
-    k = torch.from_numpy(key.view(np.int64))
-    c0 = k & _U32
-    c1 = (k >> 32) & _U32
-    z = torch.zeros_like(c0)
-    r0, _, _, _ = philox4x32(c0, c1, z, z, seed & _U32, 0x2545F491)
-    return r0.numpy().astype(np.float64) / 4294967296.0
+    on_torch = isinstance(col, torch.Tensor)
+    rp = row_ptr if on_torch else torch.from_numpy(np.ascontiguousarray(row_ptr, dtype=np.int64))
+    c = (col if on_torch else torch.from_numpy(np.ascontiguousarray(col))).to(torch.int64)
+    rp = rp.to(torch.int64)
+    n = rp.shape[0] - 1
+    src = torch.repeat_interleave(torch.arange(n, device=rp.device, dtype=torch.int64), rp[1:] - rp[:-1])
+    lo, hi = torch.minimum(src, c), torch.maximum(src, c)
+    del src, c
+    z = torch.zeros_like(lo)
+    r0, _, _, _ = philox4x32(hi, lo, z, z, seed & _U32, 0x2545F491)
+    del lo, hi, z
+    u = r0.to(torch.float64) / 4294967296.0
+    if weights is None:
+        lab = torch.clamp(torch.floor(u * n_labels).to(torch.int64), max=n_labels - 1)
+    else:
+        w = torch.as_tensor(np.asarray(weights, dtype=np.float64), device=u.device)
+        cdf = torch.cumsum(w / w.sum(), 0)
+        lab = torch.clamp(torch.searchsorted(cdf, u, right=True), max=n_labels - 1)
+    lab = lab.to(torch.uint8)
+    return lab if on_torch else lab.numpy()
+
+
+def sampled_template(g, el, n0, extra, seed):
+    """A template that matches at least once: n0 vertices reached by a
+    breadth-first walk from a random vertex of degree >= 2, the walk's tree
+    edges plus up to `extra` more edges among them, with the graph's vertex
+    and edge labels."""
+    rng = np.random.default_rng(seed)
+    deg = np.diff(g.row_ptr)
+    starts = np.nonzero(deg >= 2)[0]
+    for _ in range(100):
+        root = int(rng.choice(starts))
+        order, parent, seen = [root], {root: -1}, {root}
+        for v in order:
+            for e in range(g.row_ptr[v], g.row_ptr[v + 1]):
+                u = int(g.col[e])
+                if u not in seen and len(order) < n0:
+                    seen.add(u)
+                    parent[u] = v
+                    order.append(u)
+        if len(order) == n0:
+            break
+    idx = {v: i for i, v in enumerate(order)}
+    label_of = {}
+    for v in order:
+        for e in range(g.row_ptr[v], g.row_ptr[v + 1]):
+            u = int(g.col[e])
+            if u in idx:
+                label_of[(idx[v], idx[u])] = int(el[e]) if el is not None else 0
+    edges = [(idx[parent[v]], idx[v]) for v in order[1:]]
+    chords = [(a, b) for (a, b) in label_of if a < b and (a, b) not in edges and (b, a) not in edges]
+    rng.shuffle(chords)
+    edges += [tuple(c) for c in chords[:extra]]
+    edges = [(min(a, b), max(a, b)) for a, b in edges]
+    tel = [label_of[e] for e in edges]
+    tl = [int(g.labels[v]) for v in order]
+    return tl, edges, tel
 
 
 def label_frequencies(g: Graph, n_labels: int = 256) -> np.ndarray:

@@ -18,43 +18,6 @@ def ctx():
     return ccpm.Context(0)
 
 
-def sampled_template(g, el, n0, extra, seed):
-    """A template that matches at least once: n0 vertices reached by a
-    breadth-first walk from a random vertex of degree >= 2, the walk's tree
-    edges plus up to `extra` more edges among them, with the graph's vertex
-    and edge labels."""
-    rng = np.random.default_rng(seed)
-    deg = np.diff(g.row_ptr)
-    starts = np.nonzero(deg >= 2)[0]
-    for _ in range(100):
-        root = int(rng.choice(starts))
-        order, parent, seen = [root], {root: -1}, {root}
-        for v in order:
-            for e in range(g.row_ptr[v], g.row_ptr[v + 1]):
-                u = int(g.col[e])
-                if u not in seen and len(order) < n0:
-                    seen.add(u)
-                    parent[u] = v
-                    order.append(u)
-        if len(order) == n0:
-            break
-    idx = {v: i for i, v in enumerate(order)}
-    label_of = {}
-    for v in order:
-        for e in range(g.row_ptr[v], g.row_ptr[v + 1]):
-            u = int(g.col[e])
-            if u in idx:
-                label_of[(idx[v], idx[u])] = int(el[e]) if el is not None else 0
-    edges = [(idx[parent[v]], idx[v]) for v in order[1:]]
-    chords = [(a, b) for (a, b) in label_of if a < b and (a, b) not in edges and (b, a) not in edges]
-    rng.shuffle(chords)
-    edges += [tuple(c) for c in chords[:extra]]
-    edges = [(min(a, b), max(a, b)) for a, b in edges]
-    tel = [label_of[e] for e in edges]
-    tl = [int(g.labels[v]) for v in order]
-    return tl, edges, tel
-
-
 def check(ctx, g, tl, te, tel=None, el=None, el_on_device=False):
     from paper_1912_08453_gb300 import ccpm
     graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
@@ -97,7 +60,7 @@ def test_equals_the_first_fixpoint_of_prune(ctx):
 def test_sampled_templates_with_edge_labels(ctx, n0, extra, scale, n_el):
     g = wl.rmat_graph(scale, seed=n0 + scale)
     el = wl.edge_labels(g.row_ptr, g.col, n_el, seed=n0, weights=[8] + [1] * (n_el - 1))
-    tl, te, tel = sampled_template(g, el, n0, extra, seed=n0)
+    tl, te, tel = wl.sampled_template(g, el, n0, extra, seed=n0)
     om, st = check(ctx, g, tl, te, tel, el)
     assert st["active_v"] >= n0          # the sampled copy itself survives
 
@@ -117,7 +80,7 @@ def test_device_edge_labels_and_ragged_rows(ctx):
     # bitmap words at every offset
     g = wl.rmat_graph(13, seed=9, labels="zipf")
     el = wl.edge_labels(g.row_ptr, g.col, 4, seed=2)
-    tl, te, tel = sampled_template(g, el, 20, 5, seed=3)
+    tl, te, tel = wl.sampled_template(g, el, 20, 5, seed=3)
     check(ctx, g, tl, te, tel, el, el_on_device=True)
 
 
