@@ -10,8 +10,10 @@ two-edge tail) and 63 of its edit-distance-1/2 variants (5-9 vertices).
 One step = every template of the batch pruned end to end (init, LCC to
 fixpoint, every non-local constraint with LCC re-runs, the final
 template-driven search that makes omega* and E* exact and counts matches up to
-the count cap) with the batched entry point and the learned constraint order.
-The same templates are also pruned one at a time in the fixed order ("plain");
+the count cap) with the batched entry point (autotuned) and the learned
+constraint order where a check on a slice of the batch finds it faster than
+the fixed one.  The same templates are also pruned one at a time in the fixed
+order ("plain");
 the outputs of the two must be identical (omega words, edge-bitmap words,
 match counts), and the line reports both times.
 
@@ -27,8 +29,9 @@ e2e    = the same metric through the C ABI from pinned host buffers: graph
          edge bitmap to the host.
 Extras in the same line: the scale-25 single-template configuration (C3,
 where omega no longer fits in L2: the LCC roofline case), the scale-22
-degree-label configuration (C2), rooflines of the LCC round and of the
-searches, the CPU oracle timed on the host cores.
+degree-label configuration (C2), the LCC of a 48-vertex edge-labelled
+template (f3, 64-bit omega), rooflines of the LCC round and of the searches,
+the CPU oracle timed on the host cores.
 
 Under torchrun each rank prunes a share of the templates (dealt by
 warm-up cost, longest first; weak scaling, no collective on the data path);

@@ -2026,13 +2026,14 @@ k_edge_items(SearchArgs a, EdgeTab tab) {
     __syncthreads();
     WarpBuf<SearchItem> b{sbuf[wib], &scnt[wib], a.items, &a.st->n_items};
     b.cap = (unsigned long long)a.items_cap;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = gwarp; it < a.n_roots; it += nwarps) {
+    // one block per root: its warps take every (blockDim/32)-th window of the
+    // root's row, so the rows of hubs are split across the block
+    const int nwb = (int)(blockDim.x >> 5);
+    for (int64_t it = blockIdx.x; it < a.n_roots; it += gridDim.x) {
         const int32_t x = a.roots[it];
         const uint32_t wx = __ldg(a.om + x);
         const int64_t beg = a.rp[x], end = a.rp[x + 1];
-        for (int64_t base = beg; base < end; base += 32) {
+        for (int64_t base = beg + (int64_t)wib * 32; base < end; base += (int64_t)nwb * 32) {
             const int64_t e = base + lane;
             int32_t y = -1;
             uint32_t wy = 0u;
@@ -2040,6 +2041,8 @@ k_edge_items(SearchArgs a, EdgeTab tab) {
                 y = __ldg(a.col + e);
                 if (y > x && !((a.eb_out[e >> 5] >> (uint32_t)(e & 31)) & 1u)) wy = __ldg(a.om + y);
             }
+            // most neighbours of a hub are outside omega*: nothing to push
+            if (!__any_sync(FULL_MASK, wy != 0u)) continue;
             for (int o = 0; o < tab.n; o++) {
                 const bool ok = wy && ((wx >> tab.a[o]) & 1u) && ((wy >> tab.b[o]) & 1u);
                 SearchItem si;
@@ -3791,7 +3794,7 @@ int ccpm_prune(ccpm_ctx_t ctx, ccpm_graph_t g, ccpm_tmpl_t tm, const ccpm_option
                     a.roots = w.roots + r0;
                     a.n_roots = r1 - r0;
                     P.launches++;
-                    k_edge_items<<<grid_for(ctx, a.n_roots * 32, 256, 8), 256, 0, s>>>(a, tab);
+                    k_edge_items<<<grid_for(ctx, a.n_roots * 256, 256, 8), 256, 0, s>>>(a, tab);
                     CUF(cudaGetLastError());
                     RCF(P.read_stats());
                     a.n_items = w.st_h->n_items;
