@@ -126,11 +126,13 @@ typedef struct {
                                    /* entry, built once): 0 = when the initially   */
                                    /* active rows hold >= 1/8 of the entries and   */
                                    /* >= 2^22, 1 = always, -1 = never; same result */
-    int      grid_share;           /* ccpm_prune_batch: each worker sizes its grids */
-                                   /* for 1/grid_share of the GPU's SMs, so that  */
-                                   /* kernels of several templates run side by   */
-                                   /* side instead of one filling every SM:       */
-                                   /* 0 = the autotuned choice, 1 = the whole GPU */
+    int      grid_share;           /* ccpm_prune_batch: while k workers are busy,  */
+                                   /* each sizes its grids for 1/min(grid_share,k) */
+                                   /* of the GPU's SMs, so that kernels of several */
+                                   /* templates run side by side instead of one   */
+                                   /* filling every SM, and the last templates of */
+                                   /* a batch get the whole GPU back: 0 = the     */
+                                   /* autotuned choice, 1 = the whole GPU always  */
     ccpm_mlp_t mlp;                /* ordering network for CCPM_ORDER_LEARNED       */
 } ccpm_options;
 

@@ -526,6 +526,8 @@ typedef struct {
     uint8_t tlab[64];
     uint64_t adj[256][64];   /* adj[L][q]: template neighbours of q via edges labelled L */
     uint64_t any[64];        /* template neighbours of q, any edge label */
+    int n_used;              /* edge labels some template edge carries ... */
+    uint8_t used[256];       /* ... (adj[L] is empty for every other L) */
 } wide_tmpl_t;
 
 static int popc64(uint64_t x) { int c = 0; while (x) { x &= x - 1; c++; } return c; }
@@ -543,6 +545,11 @@ static void wide_tables(int n0, const uint8_t *tlab, int m0, const int32_t *te, 
         t->adj[L][b] |= 1ull << a;
         t->any[a] |= 1ull << b;
         t->any[b] |= 1ull << a;
+    }
+    for (int L = 0; L < 256; L++) {
+        int nonempty = 0;
+        for (int q = 0; q < n0; q++) nonempty |= t->adj[L][q] != 0;
+        if (nonempty) t->used[t->n_used++] = (uint8_t)L;
     }
 }
 
@@ -596,11 +603,15 @@ static int wide_round(int64_t n, const int64_t *rp, const int32_t *col, const ui
         for (int q = 0; q < t->n0; q++) {
             if (!((wv >> q) & 1ull)) continue;
             int ok = 1;
-            /* coverage, edge label by edge label */
-            for (int L = 0; ok && L < 256; L++)
+            /* coverage, edge label by edge label (labels no template edge
+             * carries have no template neighbours to cover) */
+            for (int i = 0; ok && i < t->n_used; i++) {
+                int L = t->used[i];
                 if (t->adj[L][q] & ~U[L]) ok = 0;
+            }
             /* distinct-neighbour multiplicity per (vertex label, edge label) */
-            for (int L = 0; ok && L < 256; L++) {
+            for (int i = 0; ok && i < t->n_used; i++) {
+                int L = t->used[i];
                 for (int b = 0; ok && b < t->n0; b++) {
                     if (!((t->adj[L][q] >> b) & 1ull)) continue;
                     uint64_t cls = 0;

@@ -243,8 +243,7 @@ class Graph:
             self.ctx.check(lib.ccpm_graph_set_edge_labels(self.h, None, CCPM_HOST_PTRS), "ccpm_graph_set_edge_labels")
             self._el = None
             return
-        if int(edge_labels.shape[0]) != self.m:
-            raise ValueError(f"edge labels hold {int(edge_labels.shape[0])} entries, the graph {self.m}")
+        check_edge_labels(edge_labels, self.m)
         p, dev = _ptr(edge_labels)
         flags = (CCPM_DEVICE_PTRS if dev else CCPM_HOST_PTRS) | (CCPM_VALIDATE if validate else 0)
         self.ctx.check(lib.ccpm_graph_set_edge_labels(self.h, p, flags), "ccpm_graph_set_edge_labels")
@@ -260,6 +259,24 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def check_edge_labels(edge_labels, m):
+    """The library reads m bytes from the array it is given: one uint8 label
+    per CSR entry, contiguous (ValueError otherwise)."""
+    import torch
+    if isinstance(edge_labels, torch.Tensor):
+        ok_type = edge_labels.dtype == torch.uint8
+        contiguous = edge_labels.is_contiguous()
+    else:
+        ok_type = isinstance(edge_labels, np.ndarray) and edge_labels.dtype == np.uint8
+        contiguous = ok_type and edge_labels.flags["C_CONTIGUOUS"]
+    if not ok_type:
+        raise ValueError("edge labels must be a uint8 numpy array or tensor")
+    if edge_labels.ndim != 1 or int(edge_labels.shape[0]) != m:
+        raise ValueError(f"edge labels hold {int(edge_labels.shape[0])} entries, the graph {m}")
+    if not contiguous:
+        raise ValueError("edge labels must be contiguous")
 
 
 def lcc_wide(ctx, graph, labels, edges, edge_labels=None):

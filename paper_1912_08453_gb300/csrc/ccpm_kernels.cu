@@ -2319,7 +2319,18 @@ struct ccpm_ctx {
     Workspace ws;                         // scratch of prunes issued on this context
     std::vector<ccpm_ctx *> workers;      // contexts of concurrent batch workers
     cudaEvent_t wait_ev = nullptr;        // batch workers: waits poll this event and yield
+    // batch workers: grids are sized for sm_total / min(batch_share, workers
+    // busy right now), so the last templates of a batch get the whole GPU back
+    const std::atomic<int> *batch_busy = nullptr;
+    int batch_share = 1;
 };
+
+// SMs a launch of this context sizes its grid for.
+int grid_sms(const ccpm_ctx *ctx) {
+    if (!ctx->batch_busy) return ctx->num_sms;
+    const int busy = std::max(1, std::min(ctx->batch_share, ctx->batch_busy->load(std::memory_order_relaxed)));
+    return std::max(1, ctx->sm_total / busy);
+}
 
 struct ccpm_graph {
     ccpm_ctx *ctx = nullptr;
@@ -2556,7 +2567,7 @@ int expand_more(ccpm_ctx *ctx, Workspace &w, SearchArgs &a, int max_depth, int64
                                 ctx->stream));
         CU(ctx, cudaMemsetAsync(&w.st->n_items, 0, sizeof(unsigned int), ctx->stream));
         launches++;
-        int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_items + 3) / 4, (int64_t)ctx->num_sms * 16));
+        int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_items + 3) / 4, (int64_t)grid_sms(ctx) * 16));
         k_expand_next<<<grid, 128, 0, ctx->stream>>>(a, w.items2, a.n_items);
         CU(ctx, cudaGetLastError());
         unsigned int n2 = 0;
@@ -2575,12 +2586,12 @@ int lcc_grid(ccpm_ctx *ctx, K kernel, int64_t warps) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
         per_sm = 4;
     int64_t need = (warps + 7) / 8;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)ctx->num_sms * per_sm));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)grid_sms(ctx) * per_sm));
 }
 
 int grid_for(ccpm_ctx *ctx, int64_t work_items, int per_block, int blocks_per_sm) {
     int64_t need = (work_items + per_block - 1) / per_block;
-    int64_t cap = (int64_t)ctx->num_sms * blocks_per_sm;
+    int64_t cap = (int64_t)grid_sms(ctx) * blocks_per_sm;
     if (need < 1) need = 1;
     return (int)std::min(need, cap);
 }
@@ -2753,7 +2764,7 @@ struct Pipeline {
         a.acc = w.acc;
         a.st = slot;
         a.prev = prev;
-        a.resident_warps = ctx->num_sms * 32;
+        a.resident_warps = grid_sms(ctx) * 32;
         a.hub_deg = w.hub_deg;
         a.deg = compact_mode >= 0 ? w.deg : nullptr;
         a.lab0 = from_labels ? g->lab : nullptr;
@@ -2767,7 +2778,7 @@ struct Pipeline {
         from_labels = false;
         // prefetch units: large enough to hide the per-vertex loads, small
         // enough that every resident warp gets several of them
-        const int64_t resident = (int64_t)ctx->num_sms * 32;
+        const int64_t resident = (int64_t)grid_sms(ctx) * 32;
         a.med_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, n_med / (4 * resident)));
         a.small_chunk = n_small >= 32 * 4 * resident ? 32 : (n_small >= 16 * 4 * resident ? 16 : 8);
         // a queued round does not know its sizes: one full resident wave
@@ -3909,19 +3920,32 @@ static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, const std::vector<int> &order
         if (cudaEventCreateWithFlags(&wk->wait_ev, cudaEventDisableTiming) != cudaSuccess)
             return set_err(ctx, CCPM_ECUDA, "batch: worker event");
     }
-    // grid share: a worker sizes its grids for 1/share of the SMs (the
-    // persistent-style search kernels would otherwise hold every SM until they
-    // finish, and the small kernels of other templates would wait behind them)
+    // grid share: while k workers are busy a worker sizes its grids for
+    // 1/min(share, k) of the SMs (the persistent-style search kernels would
+    // otherwise hold every SM until they finish, and the small kernels of
+    // other templates would wait behind them); the last templates of the
+    // batch get the whole GPU back
     const int share = std::max(1, opt->grid_share);
-    for (int i = 0; i < W; i++) {
-        ccpm_ctx *wk = ctx->workers[(size_t)i];
-        wk->num_sms = std::max(1, wk->sm_total / share);
-    }
+    std::atomic<int> busy(0);
     // workers start after everything already queued on the caller's stream
     cudaEvent_t ready;
     CU(ctx, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    CU(ctx, cudaEventRecord(ready, ctx->stream));
-    for (int i = 0; i < W; i++) CU(ctx, cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
+    if (cudaEventRecord(ready, ctx->stream) != cudaSuccess) {
+        cudaEventDestroy(ready);
+        return set_err(ctx, CCPM_ECUDA, "batch: event record");
+    }
+    for (int i = 0; i < W; i++)
+        if (cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0) != cudaSuccess) {
+            cudaEventDestroy(ready);
+            return set_err(ctx, CCPM_ECUDA, "batch: stream wait");
+        }
+    // the counter lives on this call's stack: the workers see it only
+    // while their threads run
+    for (int i = 0; i < W; i++) {
+        ccpm_ctx *wk = ctx->workers[(size_t)i];
+        wk->batch_busy = &busy;
+        wk->batch_share = share;
+    }
     std::atomic<int> next(0);
     std::atomic<int> first_err(0);
     std::atomic<int> budget(0);
@@ -3935,7 +3959,9 @@ static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, const std::vector<int> &order
             for (int i = next.fetch_add(1); i < hi; i = next.fetch_add(1)) {
                 if (first_err.load()) break;
                 const int k = order[(size_t)i];
+                busy.fetch_add(1);
                 int rc = ccpm_prune(wk, g, tmpls[k], opt, &outs[k]);
+                busy.fetch_sub(1);
                 if (rc == CCPM_EBUDGET) {
                     budget.store(1);
                 } else if (rc) {
@@ -3949,6 +3975,7 @@ static int run_batch(ccpm_ctx *ctx, ccpm_graph *g, const std::vector<int> &order
         });
     }
     for (auto &t : pool) t.join();
+    for (int i = 0; i < W; i++) ctx->workers[(size_t)i]->batch_busy = nullptr;
     cudaEventDestroy(ready);
     if (budget.load()) *budget_hit = 1;
     if (first_err.load()) return set_err(ctx, first_err.load(), "batch: " + err_msg);

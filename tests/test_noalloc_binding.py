@@ -1,9 +1,11 @@
-"""Argument checks of the binding of the allocation-free entry point.
+"""Argument checks of the binding: the arrays of the allocation-free entry
+point, and the graph's edge labels.
 
 The library trusts the sizes it is given, so the binding checks dtype, length
 and device of every array before the call; these checks run on the host and
 are tested here without a GPU (CPU tensors fail the size and dtype checks
 before the device check is reached)."""
+import numpy as np
 import pytest
 import torch
 
@@ -41,3 +43,15 @@ def test_bad_arrays_are_rejected_before_the_call(name, bad, msg):
 def test_host_tensors_are_rejected():
     with pytest.raises(ValueError, match="must be a tensor on cuda:0"):
         call(arrays())
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (np.zeros(9, dtype=np.uint8), "hold 9 entries"),
+    (np.zeros(10, dtype=np.int32), "uint8"),
+    (torch.zeros(10, dtype=torch.int64), "uint8"),
+    (np.zeros(20, dtype=np.uint8)[::2], "contiguous"),
+])
+def test_edge_label_arrays_are_checked(bad, msg):
+    # the graph's edge labels: one uint8 per CSR entry, read m bytes at a time
+    with pytest.raises(ValueError, match=msg):
+        ccpm.check_edge_labels(bad, 10)
