@@ -279,10 +279,11 @@ def check_edge_labels(edge_labels, m):
         raise ValueError("edge labels must be contiguous")
 
 
-def lcc_wide(ctx, graph, labels, edges, edge_labels=None):
+def lcc_wide(ctx, graph, labels, edges, edge_labels=None, device_out=False):
     """LCC fixpoint for templates of up to 64 vertices with edge labels
-    (ccpm_lcc_wide).  Returns (omega uint64 [n], edge bitmap uint32 words,
-    stats dict) as host arrays."""
+    (ccpm_lcc_wide).  Returns (omega [n], edge bitmap [words], stats dict):
+    host arrays (uint64, uint32), or with device_out CUDA tensors on the
+    context's device (int64 and int32 holding the same bits)."""
     lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8))
     ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
     tel = None
@@ -290,12 +291,18 @@ def lcc_wide(ctx, graph, labels, edges, edge_labels=None):
         tel = np.ascontiguousarray(np.asarray(edge_labels, dtype=np.uint8))
         if tel.shape[0] != ed.shape[0] // 2:
             raise ValueError("one edge label per template edge")
-    omega = np.zeros(max(graph.n, 1), dtype=np.uint64)
-    bits = np.zeros(max(graph.words, 1), dtype=np.uint32)
+    if device_out:
+        import torch
+        dev = f"cuda:{ctx.device}"
+        omega = torch.empty(max(graph.n, 1), dtype=torch.int64, device=dev)
+        bits = torch.empty(max(graph.words, 1), dtype=torch.int32, device=dev)
+    else:
+        omega = np.zeros(max(graph.n, 1), dtype=np.uint64)
+        bits = np.zeros(max(graph.words, 1), dtype=np.uint32)
     st = WideStats()
     ctx.check(lib.ccpm_lcc_wide(ctx.h, graph.h, int(lab.shape[0]), _ptr(lab)[0], int(ed.shape[0] // 2),
                                 _ptr(ed)[0], None if tel is None else _ptr(tel)[0], _ptr(omega)[0],
-                                _ptr(bits)[0], 0, ctypes.byref(st)), "ccpm_lcc_wide")
+                                _ptr(bits)[0], 1 if device_out else 0, ctypes.byref(st)), "ccpm_lcc_wide")
     stats = {k: getattr(st, k) for k, _ in st._fields_}
     return omega[: graph.n], bits[: graph.words], stats
 

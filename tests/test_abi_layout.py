@@ -14,6 +14,7 @@ STRUCTS = {
     "ccpm_constraint_log": "ConstraintLog",
     "ccpm_constraint_info": "ConstraintInfo",
     "ccpm_explore_variant": "ExploreVariant",
+    "ccpm_wide_stats": "WideStats",
 }
 
 

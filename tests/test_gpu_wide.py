@@ -84,6 +84,22 @@ def test_device_edge_labels_and_ragged_rows(ctx):
     check(ctx, g, tl, te, tel, el, el_on_device=True)
 
 
+def test_device_outputs(ctx):
+    # outputs written to device memory hold the same words as host outputs
+    from paper_1912_08453_gb300 import ccpm
+    g = wl.rmat_graph(12, seed=4)
+    el = wl.edge_labels(g.row_ptr, g.col, 2, seed=1)
+    tl, te, tel = wl.sampled_template(g, el, 36, 3, seed=7)
+    graph = ccpm.Graph(ctx, g.row_ptr, g.col, g.labels)
+    graph.set_edge_labels(el)
+    om_h, bits_h, st_h = ccpm.lcc_wide(ctx, graph, tl, te, tel)
+    om_d, bits_d, st_d = ccpm.lcc_wide(ctx, graph, tl, te, tel, device_out=True)
+    np.testing.assert_array_equal(om_d.cpu().numpy().view(np.uint64), om_h)
+    np.testing.assert_array_equal(bits_d.cpu().numpy().view(np.uint32), bits_h)
+    assert st_d["rounds"] == st_h["rounds"] and st_d["edges_scanned"] == st_h["edges_scanned"]
+    graph.close()
+
+
 def test_nothing_active(ctx):
     # template labels absent from the graph: one quiescent round, empty result
     g = wl.rmat_graph(10, seed=2)
