@@ -13,10 +13,11 @@
 // of Section 4.1).  With every edge label 0 these are the rules of the 32-bit
 // pipeline.
 //
-// Layout and schedule: one warp per listed vertex; its entries are read in
-// windows aligned to the 32-entry words of the edge bitmap, so lane i of a
-// window owns bit i of one word (one broadcast load of the bits, one atomic
-// to clear the failing ones).  Rounds are snapshot rounds over two omega
+// Layout and schedule: one warp per listed vertex (one block per vertex whose
+// row is longer than 1024 entries); its entries are read in windows aligned
+// to the 32-entry words of the edge bitmap, so lane i of a window owns bit i
+// of one word (one broadcast load of the bits, one atomic to clear the
+// failing ones).  Rounds are snapshot rounds over two omega
 // buffers; each round lists the vertices that were active at its start for
 // the next round, which writes 0 for those that died and drops them.  The
 // host reads one small counter block per round.  No kernel waits on another
@@ -39,6 +40,7 @@ constexpr int kWT = 64;        // template vertices
 constexpr int kWEL = 8;        // distinct edge labels one template may use
 constexpr int kWCls = 64;      // label-multiplicity classes (need >= 2)
 constexpr int kWEdges = 2016;  // 64 * 63 / 2
+constexpr int kWHub = 1024;    // rows longer than this are walked by a whole block
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // Template tables of one call (device copy, loaded into shared memory).
@@ -53,7 +55,8 @@ struct __align__(16) WideTab {
 };
 
 struct WideCounters {
-    unsigned long long n_next;     // vertices listed for the next round
+    unsigned long long n_next;     // vertices listed for the next round (rows up to kWHub entries)
+    unsigned long long n_hub_next; // ... with longer rows
     unsigned long long scanned;    // active entries read (both ends live, bit set)
     unsigned long long alive;      // active vertices read
     unsigned long long active_v, active_e;   // hand-back totals
@@ -71,6 +74,9 @@ struct WideArgs {
     const int32_t *list_in;
     int64_t n_in;
     int32_t *list_out;
+    const int32_t *hub_in;         // vertices whose rows are longer than kWHub entries
+    int64_t n_hub;
+    int32_t *hub_out;
     WideCounters *st;
     const WideTab *tab;
 };
@@ -93,47 +99,168 @@ __device__ __forceinline__ void load_tab(WideTab &dst, const WideTab *src) {
     for (int i = threadIdx.x; i < (int)(sizeof(WideTab) / 4); i += blockDim.x) d[i] = s[i];
 }
 
+// Warp-aggregated append of v (lanes with `take`) to list[*count ...].
+__device__ __forceinline__ void push_list(bool take, int32_t v, int32_t *list, unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t act = __ballot_sync(FULL, take);
+    if (!act) return;
+    unsigned long long base = 0;
+    const int leader = __ffs(act) - 1;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(act));
+    base = __shfl_sync(FULL, base, leader);
+    if (take) list[base + __popc(act & ((1u << lane) - 1u))] = v;
+}
+
 // Alg. 3: omega_0(v) = {q : l(q) = l(v)} in both snapshot buffers; every
-// initially active vertex is listed for the first round.
+// initially active vertex is listed for the first round, on the list of its
+// row length.
 __global__ void __launch_bounds__(256)
-k_wide_init(int64_t n, const uint8_t *__restrict__ lab, const uint64_t *__restrict__ lmask, uint64_t *om0,
-            uint64_t *om1, int32_t *list, WideCounters *st) {
+k_wide_init(int64_t n, const int64_t *__restrict__ rp, const uint8_t *__restrict__ lab,
+            const uint64_t *__restrict__ lmask, uint64_t *om0, uint64_t *om1, int32_t *list, int32_t *hub,
+            WideCounters *st) {
     __shared__ uint64_t sl[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) sl[i] = lmask[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = v0 + threadIdx.x;
         uint64_t w = 0;
+        bool long_row = false;
         if (v < n) {
             w = sl[lab[v]];
             om0[v] = w;
             om1[v] = w;
+            if (w) long_row = rp[v + 1] - rp[v] > kWHub;
         }
-        const uint32_t act = __ballot_sync(FULL, w != 0);
-        if (act) {
-            unsigned long long base = 0;
-            const int leader = __ffs(act) - 1;
-            if (lane == leader) base = atomicAdd(&st->n_next, (unsigned long long)__popc(act));
-            base = __shfl_sync(FULL, base, leader);
-            if (w) list[base + __popc(act & ((1u << lane) - 1u))] = (int32_t)v;
+        push_list(w != 0 && !long_row, (int32_t)v, list, &st->n_next);
+        push_list(w != 0 && long_row, (int32_t)v, hub, &st->n_hub_next);
+    }
+}
+
+// The template neighbours of omega(v) per edge-label index (every lane of
+// the warp gets them).
+__device__ __forceinline__ void nbr_masks(const WideTab &T, uint64_t wv, uint64_t (&nb)[kWEL]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kWEL; j++) nb[j] = 0;
+    for (int q = lane; q < T.n0; q += 32)
+        if ((wv >> q) & 1ull) {
+#pragma unroll
+            for (int j = 0; j < kWEL; j++)
+                if (j < T.n_el) nb[j] |= T.adj[j][q];
+        }
+#pragma unroll
+    for (int j = 0; j < kWEL; j++) nb[j] = warp_or64(nb[j]);
+}
+
+// One warp's share of a row: windows first_w, first_w + w_step, ... (each a
+// group of four 32-entry windows aligned to the bitmap words, all loaded
+// before any is used).  Per lane: the unions per edge-label index, the
+// surviving entries, the eta change; per class, the count of surviving
+// entries meeting it is added to cnt[c] by lane 0 (atomically when several
+// warps share cnt).
+__device__ __forceinline__ void scan_windows(const WideArgs &a, const WideTab &T, uint64_t wv,
+                                             const uint64_t (&nb)[kWEL], int64_t beg, int64_t end,
+                                             int64_t first_w, int64_t w_step, uint64_t (&U)[kWEL],
+                                             uint32_t &nN, uint32_t &achg, uint32_t *cnt, bool shared_cnt,
+                                             unsigned long long &scanned) {
+    constexpr int WU = 4;
+    const int lane = threadIdx.x & 31;
+    const int n_cls = T.n_cls;
+    for (int64_t w0 = first_w; (w0 << 5) < end; w0 += w_step) {
+        bool bit[WU];
+        int32_t u[WU];
+        uint8_t lb[WU];
+        uint64_t wn[WU];
+#pragma unroll
+        for (int k = 0; k < WU; k++) {
+            const int64_t e = ((w0 + k) << 5) + lane;
+            const uint32_t word = ((w0 + k) << 5) < end ? a.ebits[w0 + k] : 0u;
+            bit[k] = e >= beg && e < end && ((word >> lane) & 1u);
+        }
+#pragma unroll
+        for (int k = 0; k < WU; k++) {
+            const int64_t e = ((w0 + k) << 5) + lane;
+            u[k] = bit[k] ? a.col[e] : 0;
+            lb[k] = (bit[k] && a.el) ? a.el[e] : (uint8_t)0;
+        }
+#pragma unroll
+        for (int k = 0; k < WU; k++) wn[k] = bit[k] ? a.om_in[u[k]] : 0ull;
+#pragma unroll
+        for (int k = 0; k < WU; k++) {
+            if (((w0 + k) << 5) >= end) break;          // past the row (warp-uniform)
+            const uint64_t wu = wn[k];
+            const int j = bit[k] ? (int)T.el_index[lb[k]] : 0xFF;
+            uint64_t m = 0;
+#pragma unroll
+            for (int jj = 0; jj < kWEL; jj++)
+                if (j == jj) m = nb[jj];
+            const bool live = bit[k] && wu != 0;     // both ends active: the entry is active
+            const bool pass = live && (wu & m) != 0;
+            scanned += live ? 1ull : 0ull;
+            if (live && !pass) achg = 1;             // eta eliminates an active entry
+            if (pass) {
+                nN++;
+#pragma unroll
+                for (int jj = 0; jj < kWEL; jj++)
+                    if (j == jj) U[jj] |= wu;
+            }
+            // the bit goes with the failing entries and with those whose
+            // other end is inactive already (no change: that entry is inactive)
+            const uint32_t drop = __ballot_sync(FULL, bit[k] && !pass);
+            if (drop && lane == 0) atomicAnd(&a.ebits[w0 + k], ~drop);
+            for (int c = 0; c < n_cls; c++) {
+                if (!((wv >> T.cls_q[c]) & 1ull)) continue;
+                const uint32_t hit = __ballot_sync(FULL, pass && j == (int)T.cls_j[c] && (wu & T.cls_mask[c]) != 0);
+                if (lane == 0 && hit) {
+                    if (shared_cnt) atomicAdd(&cnt[c], (uint32_t)__popc(hit));
+                    else cnt[c] += (uint32_t)__popc(hit);
+                }
+            }
         }
     }
 }
 
-// One snapshot round over the listed vertices, one warp each.
+// The vertex rule: q stays iff every template neighbour joined by edge
+// label j lies in U[j] and every class of q has enough distinct neighbours;
+// nothing stays without a surviving entry.
+__device__ __forceinline__ uint64_t decide_wide(const WideTab &T, uint64_t wv, const uint64_t (&U)[kWEL], uint32_t nN,
+                                                const uint32_t *cnt) {
+    uint64_t keep = 0;
+    if (nN == 0) return 0;
+    for (int q = 0; q < T.n0; q++) {
+        if (!((wv >> q) & 1ull)) continue;
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < kWEL; j++)
+            if (j < T.n_el && (T.adj[j][q] & ~U[j])) ok = false;
+        for (int c = 0; c < T.n_cls && ok; c++)
+            if (T.cls_q[c] == q && cnt[c] < T.cls_need[c]) ok = false;
+        if (ok) keep |= 1ull << q;
+    }
+    return keep;
+}
+
+// One snapshot round.  Rows of at most kWHub entries: one warp each.  Longer
+// rows (list hub_in): one block each, its warps taking interleaved window
+// groups, the partial results combined in shared memory.  Every vertex
+// listed at the start of the round is listed again (the next round writes
+// its zero if it died here); a vertex stays on the list of its row length.
 __global__ void __launch_bounds__(256)
 k_wide_round(WideArgs a) {
     __shared__ WideTab T;
     __shared__ uint32_t cnt[8][kWCls];
+    __shared__ uint32_t bcnt[kWCls];
+    __shared__ unsigned long long bU[kWEL];
+    __shared__ uint32_t bN, bchg;
     load_tab(T, a.tab);
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int n_el = T.n_el, n_cls = T.n_cls;
+    const int nwb = (int)(blockDim.x >> 5);
     unsigned long long scanned = 0, alive = 0;
     unsigned int changed = 0;
+    // (1) rows up to kWHub entries, one warp each
     for (int64_t i = gw; i < a.n_in; i += nw) {
         const int32_t v = a.list_in[i];
         const uint64_t wv = a.om_in[v];
@@ -143,105 +270,80 @@ k_wide_round(WideArgs a) {
             continue;
         }
         if (lane == 0) alive++;
-        // template neighbours of omega(v) per edge-label index
         uint64_t nb[kWEL];
-#pragma unroll
-        for (int j = 0; j < kWEL; j++) nb[j] = 0;
-        for (int q = lane; q < T.n0; q += 32)
-            if ((wv >> q) & 1ull) {
-#pragma unroll
-                for (int j = 0; j < kWEL; j++)
-                    if (j < n_el) nb[j] |= T.adj[j][q];
-            }
-#pragma unroll
-        for (int j = 0; j < kWEL; j++) nb[j] = warp_or64(nb[j]);
-        for (int c = lane; c < n_cls; c += 32) cnt[wib][c] = 0;
+        nbr_masks(T, wv, nb);
+        for (int c = lane; c < T.n_cls; c += 32) cnt[wib][c] = 0;
         __syncwarp();
         const int64_t beg = a.rp[v], end = a.rp[(int64_t)v + 1];
         uint64_t U[kWEL];
 #pragma unroll
         for (int j = 0; j < kWEL; j++) U[j] = 0;
         uint32_t nN = 0, achg = 0;
-        // four windows per step: their bits, columns, edge labels and
-        // neighbour omegas are all loaded before any of them is used
-        constexpr int WU = 4;
-        for (int64_t w0 = beg >> 5; (w0 << 5) < end; w0 += WU) {
-            bool bit[WU];
-            int32_t u[WU];
-            uint8_t lb[WU];
-            uint64_t wn[WU];
-#pragma unroll
-            for (int k = 0; k < WU; k++) {
-                const int64_t e = ((w0 + k) << 5) + lane;
-                const uint32_t word = ((w0 + k) << 5) < end ? a.ebits[w0 + k] : 0u;
-                bit[k] = e >= beg && e < end && ((word >> lane) & 1u);
-            }
-#pragma unroll
-            for (int k = 0; k < WU; k++) {
-                const int64_t e = ((w0 + k) << 5) + lane;
-                u[k] = bit[k] ? a.col[e] : 0;
-                lb[k] = (bit[k] && a.el) ? a.el[e] : (uint8_t)0;
-            }
-#pragma unroll
-            for (int k = 0; k < WU; k++) wn[k] = bit[k] ? a.om_in[u[k]] : 0ull;
-#pragma unroll
-            for (int k = 0; k < WU; k++) {
-                if (((w0 + k) << 5) >= end) break;          // past the row (warp-uniform)
-                const uint64_t wu = wn[k];
-                const int j = bit[k] ? (int)T.el_index[lb[k]] : 0xFF;
-                uint64_t m = 0;
-#pragma unroll
-                for (int jj = 0; jj < kWEL; jj++)
-                    if (j == jj) m = nb[jj];
-                const bool live = bit[k] && wu != 0;     // both ends active: the entry is active
-                const bool pass = live && (wu & m) != 0;
-                scanned += live ? 1ull : 0ull;
-                if (live && !pass) achg = 1;             // eta eliminates an active entry
-                if (pass) {
-                    nN++;
-#pragma unroll
-                    for (int jj = 0; jj < kWEL; jj++)
-                        if (j == jj) U[jj] |= wu;
-                }
-                // the bit goes with the failing entries and with those whose
-                // other end is inactive already (no change: that entry is inactive)
-                const uint32_t drop = __ballot_sync(FULL, bit[k] && !pass);
-                if (drop && lane == 0) atomicAnd(&a.ebits[w0 + k], ~drop);
-                for (int c = 0; c < n_cls; c++) {
-                    if (!((wv >> T.cls_q[c]) & 1ull)) continue;
-                    const uint32_t hit = __ballot_sync(FULL, pass && j == (int)T.cls_j[c] && (wu & T.cls_mask[c]) != 0);
-                    if (lane == 0) cnt[wib][c] += (uint32_t)__popc(hit);
-                }
-            }
-        }
+        scan_windows(a, T, wv, nb, beg, end, beg >> 5, 4, U, nN, achg, cnt[wib], false, scanned);
 #pragma unroll
         for (int j = 0; j < kWEL; j++) U[j] = warp_or64(U[j]);
         nN = __reduce_add_sync(FULL, nN);
         achg = __reduce_or_sync(FULL, achg);
         __syncwarp();
-        uint64_t keep = 0;
-        if (nN > 0) {
-            for (int q = 0; q < T.n0; q++) {
-                if (!((wv >> q) & 1ull)) continue;
-                bool ok = true;
-#pragma unroll
-                for (int j = 0; j < kWEL; j++)
-                    if (j < n_el && (T.adj[j][q] & ~U[j])) ok = false;
-                for (int c = 0; c < n_cls && ok; c++)
-                    if (T.cls_q[c] == q && cnt[wib][c] < T.cls_need[c]) ok = false;
-                if (ok) keep |= 1ull << q;
-            }
-        }
+        const uint64_t keep = decide_wide(T, wv, U, nN, cnt[wib]);
         if (keep != wv || achg) changed = 1;
         if (lane == 0) {
             a.om_out[v] = keep;
-            // listed again: the next round writes its zero if it died here
             const unsigned long long pos = atomicAdd(&a.st->n_next, 1ull);
             a.list_out[pos] = v;
         }
         __syncwarp();
     }
+    // (2) longer rows, one block each (block-uniform loop)
+    for (int64_t i = blockIdx.x; i < a.n_hub; i += gridDim.x) {
+        const int32_t v = a.hub_in[i];
+        const uint64_t wv = a.om_in[v];
+        if (wv == 0) {
+            if (threadIdx.x == 0) a.om_out[v] = 0;
+            continue;
+        }
+        if (threadIdx.x == 0) alive++;
+        uint64_t nb[kWEL];
+        nbr_masks(T, wv, nb);
+        for (int c = threadIdx.x; c < T.n_cls; c += blockDim.x) bcnt[c] = 0;
+        if (threadIdx.x < kWEL) bU[threadIdx.x] = 0ull;
+        if (threadIdx.x == 0) { bN = 0; bchg = 0; }
+        __syncthreads();
+        const int64_t beg = a.rp[v], end = a.rp[(int64_t)v + 1];
+        uint64_t U[kWEL];
+#pragma unroll
+        for (int j = 0; j < kWEL; j++) U[j] = 0;
+        uint32_t nN = 0, achg = 0;
+        scan_windows(a, T, wv, nb, beg, end, (beg >> 5) + 4 * wib, 4 * nwb, U, nN, achg, bcnt, true, scanned);
+#pragma unroll
+        for (int j = 0; j < kWEL; j++) U[j] = warp_or64(U[j]);
+        nN = __reduce_add_sync(FULL, nN);
+        achg = __reduce_or_sync(FULL, achg);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < kWEL; j++)
+                if (U[j]) atomicOr(&bU[j], (unsigned long long)U[j]);
+            if (nN) atomicAdd(&bN, nN);
+            if (achg) atomicOr(&bchg, 1u);
+        }
+        __syncthreads();
+        if (wib == 0) {
+            uint64_t Ub[kWEL];
+#pragma unroll
+            for (int j = 0; j < kWEL; j++) Ub[j] = bU[j];
+            const uint64_t keep = decide_wide(T, wv, Ub, bN, bcnt);
+            if (keep != wv || bchg) changed = 1;
+            if (lane == 0) {
+                a.om_out[v] = keep;
+                const unsigned long long pos = atomicAdd(&a.st->n_hub_next, 1ull);
+                a.hub_out[pos] = v;
+            }
+        }
+        __syncthreads();                          // bcnt / bU / bN are reused
+    }
     scanned = warp_sum64(scanned);
+    alive = warp_sum64(alive);
+    changed = __reduce_or_sync(FULL, changed);
     if (lane == 0) {
         if (scanned) atomicAdd(&a.st->scanned, scanned);
         if (alive) atomicAdd(&a.st->alive, alive);
@@ -367,13 +469,14 @@ struct WideBufs {
     uint64_t *lmask = nullptr;
     uint64_t *om[2] = {nullptr, nullptr};
     int32_t *list[2] = {nullptr, nullptr};
+    int32_t *hub[2] = {nullptr, nullptr};
     uint32_t *bits = nullptr;
     WideCounters *st = nullptr;
     WideCounters *st_h = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     ~WideBufs() {
         cudaFree(tab); cudaFree(lmask); cudaFree(om[0]); cudaFree(om[1]);
-        cudaFree(list[0]); cudaFree(list[1]); cudaFree(bits); cudaFree(st);
+        cudaFree(list[0]); cudaFree(list[1]); cudaFree(hub[0]); cudaFree(hub[1]); cudaFree(bits); cudaFree(st);
         if (st_h) cudaFreeHost(st_h);
         for (auto e : ev) if (e) cudaEventDestroy(e);
     }
@@ -413,6 +516,7 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
     for (int i = 0; i < 2; i++) {
         WCU(cudaMalloc(&B.om[i], sizeof(uint64_t) * (size_t)std::max<int64_t>(n, 1)), "alloc");
         WCU(cudaMalloc(&B.list[i], sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)), "alloc");
+        WCU(cudaMalloc(&B.hub[i], sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)), "alloc");
     }
     WCU(cudaMalloc(&B.bits, sizeof(uint32_t) * (size_t)std::max<int64_t>(words, 1)), "alloc");
     WCU(cudaMalloc(&B.st, sizeof(WideCounters)), "alloc");
@@ -427,11 +531,12 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
         k_wide_fill<<<grid_of(ctx, words, 256, 8), 256, 0, s>>>(words, m, B.bits);
         WCU(cudaGetLastError(), "launch");
     }
-    k_wide_init<<<grid_of(ctx, n, 256, 8), 256, 0, s>>>(n, G.lab, B.lmask, B.om[0], B.om[1], B.list[0], B.st);
+    k_wide_init<<<grid_of(ctx, n, 256, 8), 256, 0, s>>>(n, G.rp, G.lab, B.lmask, B.om[0], B.om[1], B.list[0],
+                                                         B.hub[0], B.st);
     WCU(cudaGetLastError(), "launch");
     WCU(cudaMemcpyAsync(B.st_h, B.st, sizeof(WideCounters), cudaMemcpyDeviceToHost, s), "copy");
     WCU(cudaStreamSynchronize(s), "sync");
-    int64_t n_in = (int64_t)B.st_h->n_next;
+    int64_t n_in = (int64_t)B.st_h->n_next, n_hub = (int64_t)B.st_h->n_hub_next;
     int64_t rounds = 0, scanned = 0, alive = 0;
     int cur = 0, li = 0;
     for (;;) {
@@ -446,9 +551,13 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
         a.list_in = B.list[li];
         a.n_in = n_in;
         a.list_out = B.list[li ^ 1];
+        a.hub_in = B.hub[li];
+        a.n_hub = n_hub;
+        a.hub_out = B.hub[li ^ 1];
         a.st = B.st;
         a.tab = B.tab;
-        k_wide_round<<<grid_of(ctx, n_in * 32, 256, 8), 256, 0, s>>>(a);
+        const int grid = std::max(grid_of(ctx, n_in * 32, 256, 8), grid_of(ctx, n_hub * 256, 256, 8));
+        k_wide_round<<<grid, 256, 0, s>>>(a);
         WCU(cudaGetLastError(), "launch");
         WCU(cudaMemcpyAsync(B.st_h, B.st, sizeof(WideCounters), cudaMemcpyDeviceToHost, s), "copy");
         WCU(cudaStreamSynchronize(s), "sync");
@@ -458,6 +567,7 @@ extern "C" int ccpm_lcc_wide(ccpm_ctx_t ctx, ccpm_graph_t g, int n0, const uint8
         cur ^= 1;                  // omega of the round just run
         li ^= 1;
         n_in = (int64_t)B.st_h->n_next;
+        n_hub = (int64_t)B.st_h->n_hub_next;
         if (!B.st_h->changed) break;
     }
     WCU(cudaMemsetAsync(B.st, 0, sizeof(WideCounters), s), "memset");
