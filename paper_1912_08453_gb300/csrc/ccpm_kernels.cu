@@ -24,8 +24,6 @@
 #include <string>
 #include <vector>
 
-#include <cub/device/device_scan.cuh>
-#include <cub/device/device_segmented_sort.cuh>
 
 #include <atomic>
 #include <climits>
@@ -2120,6 +2118,148 @@ k_gather_labels(int64_t m, const int32_t *__restrict__ col, const uint8_t *__res
         out[e] = __ldg(lab + __ldg(col + e));
 }
 
+// Label-grouped rows (once per graph): every row's entries stably sorted by
+// their neighbour's label, by a counting sort per row.  One warp per row: a
+// histogram of the row's labels in shared memory (256 bins), its exclusive
+// scan, then the entries in order, 32 at a time, each placed at its label's
+// next slot (lanes with equal labels are ranked by lane order, so equal
+// labels keep their order).  keys: the labels in entry order, or NULL to
+// gather them.
+__device__ __forceinline__ uint32_t row_label(const uint8_t *keys, const int32_t *col, const uint8_t *lab,
+                                              int64_t e, int64_t end) {
+    if (e >= end) return 256u;                    // no entry: a value no label has
+    return keys ? (uint32_t)keys[e] : (uint32_t)__ldg(lab + __ldg(col + e));
+}
+
+__global__ void __launch_bounds__(256)
+k_label_sort(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+             const uint8_t *__restrict__ lab, const uint8_t *__restrict__ keys, uint8_t *nlab, int32_t *lcol) {
+    __shared__ uint32_t bins[8][256];
+    const int wib = threadIdx.x >> 5;
+    const int lane = (int)lane_id();
+    uint32_t *h = bins[wib];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = gw; v < n; v += nw) {
+        const int64_t beg = rp[v], end = rp[v + 1];
+        if (end <= beg) continue;
+#pragma unroll
+        for (int k = 0; k < 8; k++) h[lane * 8 + k] = 0u;
+        __syncwarp();
+        for (int64_t c = beg; c < end; c += 32) {
+            const uint32_t L = row_label(keys, col, lab, c + lane, end);
+            const uint32_t grp = __match_any_sync(FULL_MASK, L);
+            if (L < 256u && lane == __ffs(grp) - 1) h[L] += (uint32_t)__popc(grp);
+            __syncwarp();
+        }
+        // exclusive scan of the 256 bins: 8 per lane, then across lanes
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) { loc[k] = sum; sum += h[lane * 8 + k]; }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - sum;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) h[lane * 8 + k] = excl + loc[k];
+        __syncwarp();
+        for (int64_t c = beg; c < end; c += 32) {
+            const int64_t e = c + lane;
+            const uint32_t L = row_label(keys, col, lab, e, end);
+            const uint32_t grp = __match_any_sync(FULL_MASK, L);
+            if (L < 256u) {
+                const uint32_t below = grp & ((1u << lane) - 1u);
+                const int64_t pos = beg + (int64_t)h[L] + __popc(below);
+                nlab[pos] = (uint8_t)L;
+                lcol[pos] = __ldg(col + e);
+            }
+            __syncwarp();
+            if (L < 256u && lane == __ffs(grp) - 1) h[L] += (uint32_t)__popc(grp);
+            __syncwarp();
+        }
+    }
+}
+
+// Exclusive prefix sum of n int64 values, in three passes: each block scans
+// a tile of kScanTile values and writes its total, one block scans the tile
+// totals (in tiles of its own, carrying the running sum), and each tile adds
+// its offset.
+constexpr int kScanTile = 2048;                 // 256 threads x 8 values
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t &total) {
+    __shared__ int64_t warp_tot[8];
+    const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wib] = incl;
+    __syncthreads();
+    int64_t before = 0;
+    total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        if (w < wib) before += warp_tot[w];
+        total += warp_tot[w];
+    }
+    __syncthreads();
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(256)
+k_scan_tiles(int64_t n, const int64_t *__restrict__ in, int64_t *out, int64_t *tile_sum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * 8;
+    int64_t v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(s, total);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256)
+k_scan_sums(int64_t tiles, int64_t *tile_sum) {
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < tiles; t0 += kScanTile) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * 8;
+        int64_t v[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            v[k] = base + k < tiles ? tile_sum[base + k] : 0;
+            s += v[k];
+        }
+        int64_t total;
+        int64_t run = carry + block_excl_scan(s, total);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (base + k < tiles) tile_sum[base + k] = run;
+            run += v[k];
+        }
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_scan_add(int64_t n, int64_t *out, const int64_t *__restrict__ tile_off) {
+    const int64_t off = tile_off[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (base + i < n) out[base + i] += off;
+}
+
 // Roots of a search: every vertex whose omega meets `heads`.
 __global__ void __launch_bounds__(256)
 k_collect_roots(int64_t n, const uint32_t *__restrict__ om, uint32_t heads, int32_t *roots, RoundStats *st) {
@@ -2507,30 +2647,34 @@ int ensure_label_rows(ccpm_ctx *ctx, ccpm_graph *g) {
     std::lock_guard<std::mutex> lock(g->lrow_mu);
     if (g->lcol || g->m == 0) return CCPM_OK;
     int rc;
-    uint8_t *keys = g->elab;        // the entry labels are the sort keys (gathered here if not built)
     if ((rc = dalloc(ctx, &g->lcol, (size_t)g->m))) return rc;
-    if ((rc = dalloc(ctx, &g->nlab, (size_t)g->m))) return rc;
-    if (!keys) {
-        if ((rc = dalloc(ctx, &keys, (size_t)g->m))) return rc;
-        int grid = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
-        k_gather_labels<<<grid, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, keys);
+    if ((rc = dalloc(ctx, &g->nlab, (size_t)g->m))) {
+        cudaFree(g->lcol);
+        g->lcol = nullptr;
+        return rc;
     }
-    size_t tmp_bytes = 0;
-    cudaError_t e = cub::DeviceSegmentedSort::StableSortPairs(nullptr, tmp_bytes, keys, g->nlab, g->col, g->lcol,
-                                                              g->m, g->n, g->rp, g->rp + 1, ctx->stream);
-    void *tmp = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes ? tmp_bytes : 1);
-    if (e == cudaSuccess)
-        e = cub::DeviceSegmentedSort::StableSortPairs(tmp, tmp_bytes, keys, g->nlab, g->col, g->lcol,
-                                                      g->m, g->n, g->rp, g->rp + 1, ctx->stream);
+    // a counting sort of every row by neighbour label; its keys are the entry
+    // labels (gathered here into a temporary array when they are not built:
+    // the sort reads them twice)
+    uint8_t *keys = g->elab;
+    if (!keys) {
+        if ((rc = dalloc(ctx, &keys, (size_t)g->m))) {
+            cudaFree(g->lcol); cudaFree(g->nlab);
+            g->lcol = nullptr; g->nlab = nullptr;
+            return rc;
+        }
+        const int gg = (int)std::min<int64_t>((g->m + 255) / 256, (int64_t)ctx->num_sms * 8);
+        k_gather_labels<<<gg, 256, 0, ctx->stream>>>(g->m, g->col, g->lab, keys);
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, (int64_t)grid_sms(ctx) * 8));
+    k_label_sort<<<grid, 256, 0, ctx->stream>>>(g->n, g->rp, g->col, g->lab, keys, g->nlab, g->lcol);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(tmp);
     if (keys != g->elab) cudaFree(keys);
     if (e != cudaSuccess) {
         cudaFree(g->lcol); cudaFree(g->nlab);
         g->lcol = nullptr; g->nlab = nullptr;
-        return set_err(ctx, e == cudaErrorMemoryAllocation ? CCPM_ENOMEM : CCPM_ECUDA,
-                       std::string("label-grouped rows: ") + cudaGetErrorString(e));
+        return set_err(ctx, CCPM_ECUDA, std::string("label-grouped rows: ") + cudaGetErrorString(e));
     }
     g->lrows_ready.store(true);
     return CCPM_OK;
@@ -3002,9 +3146,11 @@ struct Pipeline {
         }
         ca.piece_cnt = w.piece_cnt;
         // offsets of the new rows from the entries each vertex kept in the last
-        // round (0 for every vertex that is not live)
-        size_t tmp = 0;
-        CU(ctx, cub::DeviceScan::ExclusiveSum(nullptr, tmp, w.deg, w.sub_rp[nb], g->n + 1, s));
+        // round (0 for every vertex that is not live): exclusive prefix sum of
+        // the kept counts (tile scans, a scan of the tile totals, the tile
+        // offsets added)
+        const int64_t cnt = g->n + 1, tiles = (cnt + kScanTile - 1) / kScanTile;
+        const size_t tmp = sizeof(int64_t) * (size_t)tiles;
         if (tmp > w.scan_tmp_bytes) {
             cudaFree(w.scan_tmp);
             w.scan_tmp = nullptr;
@@ -3012,8 +3158,12 @@ struct Pipeline {
             CU(ctx, cudaMalloc(&w.scan_tmp, tmp));
             w.scan_tmp_bytes = tmp;
         }
-        launches++;
-        CU(ctx, cub::DeviceScan::ExclusiveSum(w.scan_tmp, tmp, w.deg, w.sub_rp[nb], g->n + 1, s));
+        int64_t *tile_sum = (int64_t *)w.scan_tmp;
+        launches += 3;
+        k_scan_tiles<<<(unsigned)tiles, 256, 0, s>>>(cnt, w.deg, w.sub_rp[nb], tile_sum);
+        k_scan_sums<<<1, 256, 0, s>>>(tiles, tile_sum);
+        k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(cnt, w.sub_rp[nb], tile_sum);
+        CU(ctx, cudaGetLastError());
         if (n_chunk > 0) {
             launches++;
             k_compact_count<<<grid_for(ctx, n_chunk * 32, 256, 8), 256, 0, s>>>(ca);
