@@ -22,6 +22,10 @@
  *     undirected edge always carry the same value.
  *   - Calls run on the context's CUDA stream and return after the work they
  *     describe has completed, unless stated otherwise.
+ *   - Calls that take a context (or a graph, template or result made with
+ *     one) make the context's device current on the calling thread and leave
+ *     it current; ccpm_lcc_fixpoint_noalloc, which takes no context, restores
+ *     the caller's current device.
  *   - All handles are single-thread objects: do not use one handle from two
  *     host threads at once.
  */
