@@ -147,9 +147,9 @@ def test_edge_label_breaks_a_triangle():
     g, el = graph_of(3, [(0, 1), (1, 2), (0, 2)], [0, 1, 2], {(0, 1): 1, (1, 2): 1, (0, 2): 2})
     og = oracle.Graph(g.row_ptr, g.col, g.labels)
     om, A, rounds, _ = oracle.wide_lcc(og, tl, te, tel, el)
-    # round 1: entries (0,2) and (2,0) fail eta, so vertices 0 and 2 lose the
-    # only neighbour that could cover them; round 2: vertex 1 has no live
-    # neighbour left; round 3 changes nothing
+    # first LCC round: entries (0,2) and (2,0) fail eta, so vertices 0 and 2
+    # lose the only neighbour that could cover them; second: vertex 1 has no
+    # live neighbour left; the third changes nothing
     assert not om.any() and not A.any()
     assert rounds == 3
     # the same graph with every edge labelled 1 matches
