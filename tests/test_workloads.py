@@ -80,3 +80,31 @@ def test_random_templates_connected_and_variants_bounded():
     assert vs == wl.edit_variants(base, 40, seed=5, label_pool=[5, 7, 11, 12])
     for v in vs:
         assert 5 <= v.n0 <= 9 and wl.is_connected(v.n0, v.edges)
+
+
+def test_edge_labels_symmetric_seeded_and_weighted():
+    g = wl.rmat_graph(10, seed=2)
+    el = wl.edge_labels(g.row_ptr, g.col, 4, seed=5)
+    assert el.dtype == np.uint8 and el.shape[0] == g.m_dir and el.max() < 4
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    lab = {(int(a), int(b)): int(x) for a, b, x in zip(src, g.col, el)}
+    assert all(lab[(b, a)] == x for (a, b), x in lab.items())      # both entries of an edge agree
+    assert np.array_equal(el, wl.edge_labels(g.row_ptr, g.col, 4, seed=5))
+    assert not np.array_equal(el, wl.edge_labels(g.row_ptr, g.col, 4, seed=6))
+    w = wl.edge_labels(g.row_ptr, g.col, 3, seed=5, weights=[8, 1, 1])
+    f = np.bincount(w, minlength=3) / len(w)
+    assert abs(f[0] - 0.8) < 0.03 and f[1] > 0.05 and f[2] > 0.05
+
+
+def test_sampled_template_is_a_subgraph_of_the_graph():
+    g = wl.rmat_graph(10, seed=3)
+    el = wl.edge_labels(g.row_ptr, g.col, 3, seed=1)
+    for n0, extra in ((5, 0), (12, 3), (40, 6)):
+        tl, te, tel = wl.sampled_template(g, el, n0, extra, seed=n0)
+        assert len(tl) == n0 and wl.is_connected(n0, te) and len(te) >= n0 - 1
+        assert len(set(te)) == len(te) and all(a < b for a, b in te)
+        assert len(tel) == len(te) and set(tl) <= set(int(x) for x in g.labels)
+        # the sampled copy itself is a match, so the LCC fixpoint keeps at least n0 vertices
+        import oracle
+        om, _, _, _ = oracle.wide_lcc(oracle.Graph(g.row_ptr, g.col, g.labels), tl, te, tel, el)
+        assert int((om != 0).sum()) >= n0
